@@ -1,0 +1,514 @@
+/*
+ * oracle.c -- plain, slow FP64 CPU reference of the adaptive dual-weight
+ * gravitational denoiser of arXiv 2512.10386 (Sec. 3, Eq. 10-22).
+ *
+ * TEST INFRASTRUCTURE ONLY: the checker the GPU library is compared against.
+ * Only the test-suite, the smoke check and the benchmark's CPU-baseline leg
+ * may call it.  It shares no code with the CUDA library.
+ *
+ * Arithmetic: FP64 everywhere, except where a step is *defined* on FP32 values
+ * so that its integer outcome (Morton key, voxel index, neighbour order,
+ * density-gate rank) is reproducible bit for bit on any IEEE machine.  Those
+ * steps spell out every FP32 operation; the file must be compiled with
+ * -ffp-contract=off and without fast-math so no operation is fused or
+ * reordered.  Algorithms are the obvious ones: qsort for every ordering,
+ * brute force for every count and every neighbour search.
+ *
+ * Readings of the paper where it is silent, garbled or ambiguous (each one
+ * also listed in the design notes):
+ *  R1 root cube: axis-aligned bounding cube anchored at the FP32 minimum,
+ *     side = largest FP32 extent (1 if all points coincide); coordinates are
+ *     quantised to 21 bits per axis, q = min(2^21-1, floor((x-lo)*s)),
+ *     s = 2^21/side, all in FP32.
+ *  R2 octree: node (level L, top 3L key bits) is a leaf iff it holds at most
+ *     leaf_capacity points or L = max_depth (the minimum-side rule); empty
+ *     children are skipped; leaves are numbered in Morton order.
+ *  R3 leaf extents are floored at delta = side*2^-21 per axis so that flat or
+ *     colinear leaves keep V_t > 0 (Eq. 10).
+ *  R4 Eq. 11's cube root is the fixed Newton sequence of orc_cbrt_spec.
+ *  R5 voxel grid origin = leaf bounding-box minimum; voxel index per axis
+ *     floor((x-lo_t)/h) in FP32, saturated at 2^21-1; Eq. 12 uses ">= n_v".
+ *  R6 kNN searches the leaf's P_1 only, excludes the point itself, uses
+ *     k_eff = min(K, |P_1|-1) (a leaf with |P_1| <= 1 loses its points at the
+ *     density gate), d^2 = fma(dz,dz,fma(dy,dy,dx*dx)) in FP32 with
+ *     dx = x_j - x_i, and orders candidates by (d^2, input index).
+ *  R7 r_K^2 is the k_eff-th squared distance floored at delta^2 (FP32);
+ *     Eq. 13 uses k_eff for K.
+ *  R8 Eq. 14: q is in percent (MATLAB prctile units); prctile is taken per
+ *     leaf over P_1 and evaluated exactly: keep rho_i >= rho_(c) with
+ *     c = clamp(ceil(n*q/100 + 0.5), 1, n) on ascending rho, which is what
+ *     the hazen-interpolated percentile gives in exact arithmetic.
+ *  R9 Eq. 16: rho_med is the median over the leaf's P_2 (mean of the two
+ *     middle values for an even count).
+ *  R10 Eq. 21 reuses the single kNN pass on P_1: N_K(i), r_K and rho_j come
+ *     from it, so a neighbour j may lie outside P_2.  Eq. 20 is generalised
+ *     to 1/((d^2)^(gamma/2) + eps_k); gamma = 2 is the paper's kernel.
+ *     Scores are summed in FP64 in neighbour order.
+ *  R11 Top-lambda (end of Sec. 3): keep ceil(lambda*|P_2|) points of each
+ *     leaf by (F descending, input index ascending).  Mode 1 instead keeps
+ *     ln F >= tau (the differentiable form).
+ *  R12 differentiable form: removal probability r_i = 1 - sigmoid((ln F_i -
+ *     tau)/T) on P_2 and 1 elsewhere; soft-F1 = 2 sum(r y)/(sum r + sum y)
+ *     (Eq. 26-28 with soft counts); loss = 1 - soft-F1.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define QMAX 2097151u                    /* 2^21 - 1                      */
+#define INV_TWO21 4.76837158203125e-07f  /* 2^-21, exact in FP32          */
+#define NONE32 0xFFFFFFFFu
+#define PI_D 3.14159265358979323846
+
+/* ------------------------------------------------------------------ */
+/* orderings (qsort comparators)                                       */
+/* ------------------------------------------------------------------ */
+typedef struct { uint64_t key; uint32_t idx; } keyed_t;
+
+static int cmp_keyed(const void *a, const void *b) {
+  const keyed_t *x = (const keyed_t *)a, *y = (const keyed_t *)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
+  return 0;
+}
+
+typedef struct { float d2; uint32_t idx; uint32_t pos; } cand_t;
+
+static int cmp_cand(const void *a, const void *b) {
+  const cand_t *x = (const cand_t *)a, *y = (const cand_t *)b;
+  if (x->d2 != y->d2) return x->d2 < y->d2 ? -1 : 1;
+  if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
+  return 0;
+}
+
+static int cmp_double(const void *a, const void *b) {
+  double x = *(const double *)a, y = *(const double *)b;
+  return (x < y) ? -1 : (x > y) ? 1 : 0;
+}
+
+typedef struct { double f; uint32_t idx; uint32_t pos; } ranked_t;
+
+static int cmp_ranked(const void *a, const void *b) {  /* F desc, index asc */
+  const ranked_t *x = (const ranked_t *)a, *y = (const ranked_t *)b;
+  if (x->f != y->f) return x->f > y->f ? -1 : 1;
+  if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* R1: Morton keys                                                     */
+/* ------------------------------------------------------------------ */
+uint64_t orc_interleave(uint32_t qx, uint32_t qy, uint32_t qz) {
+  uint64_t key = 0;
+  for (int b = 0; b < 21; ++b) {
+    key |= (uint64_t)((qx >> b) & 1u) << (3 * b + 2);
+    key |= (uint64_t)((qy >> b) & 1u) << (3 * b + 1);
+    key |= (uint64_t)((qz >> b) & 1u) << (3 * b);
+  }
+  return key;
+}
+
+static uint32_t quantise(float x, float lo, float s) {
+  float d = x - lo;
+  float t = d * s;
+  float f = floorf(t);
+  return (f < 2097151.0f) ? (uint32_t)f : QMAX;
+}
+
+/* ------------------------------------------------------------------ */
+/* R4: cube root for Eq. 11.  u = m * 2^e with m in [0.5, 1) (frexp);  */
+/* start at y = 2^floor(e/3) and take 10 Newton steps on y^3 - u = 0,   */
+/* y <- y - (y*y*y - u) / (3*(y*y)), each operation rounded in FP64.    */
+/* ------------------------------------------------------------------ */
+double orc_cbrt_spec(double u) {
+  int e = 0;
+  (void)frexp(u, &e);
+  int k = (e >= 0) ? e / 3 : -((-e + 2) / 3);
+  double y = ldexp(1.0, k);
+  for (int it = 0; it < 10; ++it) {
+    double y2 = y * y;
+    double y3 = y2 * y;
+    double num = y3 - u;
+    double den = 3.0 * y2;
+    y = y - num / den;
+  }
+  return y;
+}
+
+/* ------------------------------------------------------------------ */
+/* R2: octree leaves over the sorted keys (recursive, top-down)        */
+/* ------------------------------------------------------------------ */
+typedef struct { uint32_t start, count, level; } leaf_t;
+
+typedef struct {
+  const keyed_t *sorted;
+  uint32_t cap, max_depth;
+  leaf_t *leaves;
+  int64_t n_leaves;
+} octree_t;
+
+static void octree_build(octree_t *o, uint32_t level, uint32_t begin, uint32_t end) {
+  uint32_t count = end - begin;
+  if (count <= o->cap || level == o->max_depth) {
+    leaf_t lf = {begin, count, level};
+    o->leaves[o->n_leaves++] = lf;
+    return;
+  }
+  int shift = 3 * (21 - (int)(level + 1));  /* child triple of level+1 */
+  uint32_t i = begin;
+  for (uint32_t c = 0; c < 8; ++c) {
+    uint32_t j = i;
+    while (j < end && (uint32_t)((o->sorted[j].key >> shift) & 7u) == c) ++j;
+    if (j > i) octree_build(o, level + 1, i, j);
+    i = j;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* per-leaf pipeline                                                   */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  const float *xyz;
+  const orc_params *p;
+  float delta;         /* side * 2^-21 */
+  orc_out *out;
+  double *dF;          /* [n][3] dF/d(alpha, sigma, gamma), or NULL */
+  double *F_all;       /* [n] scores (internal, always filled)     */
+  uint8_t *stage_all;  /* [n] stages (internal, always filled)     */
+} ctx_t;
+
+static float coord(const ctx_t *c, uint32_t i, int a) { return c->xyz[3 * (size_t)i + a]; }
+
+static float sq_dist(const ctx_t *c, uint32_t i, uint32_t j) {
+  float dx = coord(c, j, 0) - coord(c, i, 0);
+  float dy = coord(c, j, 1) - coord(c, i, 1);
+  float dz = coord(c, j, 2) - coord(c, i, 2);
+  float xx = dx * dx;
+  return fmaf(dz, dz, fmaf(dy, dy, xx));
+}
+
+static int process_leaf(ctx_t *c, const keyed_t *sorted, const leaf_t *lf, uint32_t leaf_id) {
+  const orc_params *p = c->p;
+  orc_out *o = c->out;
+  const uint32_t nt = lf->count;
+  uint32_t *idx = (uint32_t *)malloc(sizeof(uint32_t) * nt);
+  uint32_t *vox = (uint32_t *)malloc(sizeof(uint32_t) * nt * 3);
+  uint32_t *cnt = (uint32_t *)malloc(sizeof(uint32_t) * nt);
+  uint32_t *p1 = (uint32_t *)malloc(sizeof(uint32_t) * nt);
+  if (!idx || !vox || !cnt || !p1) return ORC_ENOMEM;
+  for (uint32_t t = 0; t < nt; ++t) idx[t] = sorted[lf->start + t].idx;
+
+  /* Eq. 10 with R3: leaf bounding box, extents floored at delta */
+  float lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) { lo[a] = coord(c, idx[0], a); hi[a] = lo[a]; }
+  for (uint32_t t = 1; t < nt; ++t)
+    for (int a = 0; a < 3; ++a) {
+      float v = coord(c, idx[t], a);
+      if (v < lo[a]) lo[a] = v;
+      if (v > hi[a]) hi[a] = v;
+    }
+  float H[3];
+  for (int a = 0; a < 3; ++a) {
+    H[a] = hi[a] - lo[a];
+    if (H[a] < c->delta) H[a] = c->delta;
+  }
+  double V = (double)H[0] * (double)H[1] * (double)H[2];
+  /* Eq. 11 with R4 */
+  double u = V / (double)nt;
+  float h = (float)((double)p->beta * orc_cbrt_spec(u));
+
+  /* Eq. 12 with R5: voxel indices, occupancy by brute-force comparison */
+  for (uint32_t t = 0; t < nt; ++t)
+    for (int a = 0; a < 3; ++a) {
+      float d = coord(c, idx[t], a) - lo[a];
+      float q = d / h;
+      float f = floorf(q);
+      vox[3 * t + a] = (f < 2097151.0f) ? (uint32_t)f : QMAX;
+    }
+  uint32_t n1 = 0;
+  for (uint32_t t = 0; t < nt; ++t) {
+    uint32_t k = 0;
+    for (uint32_t s = 0; s < nt; ++s)
+      k += (vox[3 * s] == vox[3 * t] && vox[3 * s + 1] == vox[3 * t + 1] &&
+            vox[3 * s + 2] == vox[3 * t + 2]);
+    cnt[t] = k;
+    if (o->vox_count) o->vox_count[idx[t]] = k;
+    if (o->leaf_of) o->leaf_of[idx[t]] = leaf_id;
+    if (k >= p->min_vox_count) p1[n1++] = idx[t];
+    else c->stage_all[idx[t]] = 1;
+  }
+  if (o->leaf_lo) for (int a = 0; a < 3; ++a) o->leaf_lo[3 * (size_t)leaf_id + a] = lo[a];
+  if (o->leaf_h) o->leaf_h[leaf_id] = h;
+  if (o->leaf_n1) o->leaf_n1[leaf_id] = n1;
+  if (o->leaf_n2) o->leaf_n2[leaf_id] = 0;
+  if (o->leaf_rho_med) o->leaf_rho_med[leaf_id] = 0.0;
+
+  if (n1 <= 1) {  /* R6: not enough support for a neighbour */
+    for (uint32_t t = 0; t < n1; ++t) c->stage_all[p1[t]] = 2;
+    free(idx); free(vox); free(cnt); free(p1);
+    return ORC_OK;
+  }
+
+  /* kNN on P_1 (R6, R7) */
+  const uint32_t keff = (p->k < n1 - 1) ? p->k : n1 - 1;
+  uint32_t *nb = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n1 * keff);   /* P_1 positions */
+  float *nd2 = (float *)malloc(sizeof(float) * (size_t)n1 * keff);
+  float *r2 = (float *)malloc(sizeof(float) * n1);
+  double *rho = (double *)malloc(sizeof(double) * n1);
+  cand_t *cand = (cand_t *)malloc(sizeof(cand_t) * n1);
+  if (!nb || !nd2 || !r2 || !rho || !cand) return ORC_ENOMEM;
+  const float delta2 = c->delta * c->delta;
+  for (uint32_t a = 0; a < n1; ++a) {
+    uint32_t m = 0;
+    for (uint32_t b = 0; b < n1; ++b) {
+      if (b == a) continue;
+      cand[m].d2 = sq_dist(c, p1[a], p1[b]);
+      cand[m].idx = p1[b];
+      cand[m].pos = b;
+      ++m;
+    }
+    qsort(cand, m, sizeof(cand_t), cmp_cand);
+    for (uint32_t s = 0; s < keff; ++s) {
+      nb[(size_t)a * keff + s] = cand[s].pos;
+      nd2[(size_t)a * keff + s] = cand[s].d2;
+    }
+    float rk2 = cand[keff - 1].d2;
+    r2[a] = (rk2 < delta2) ? delta2 : rk2;
+    /* Eq. 13 */
+    double rr = (double)r2[a];
+    rho[a] = (double)keff / ((4.0 / 3.0) * PI_D * (rr * sqrt(rr)));
+    if (o->r2) o->r2[p1[a]] = r2[a];
+    if (o->rho) o->rho[p1[a]] = rho[a];
+    if (o->nbr)
+      for (uint32_t s = 0; s < p->k; ++s)
+        o->nbr[(size_t)p1[a] * p->k + s] = (s < keff) ? cand[s].idx : NONE32;
+    if (o->nbr_d2)
+      for (uint32_t s = 0; s < p->k; ++s)
+        o->nbr_d2[(size_t)p1[a] * p->k + s] = (s < keff) ? cand[s].d2 : 0.0f;
+  }
+
+  /* Eq. 14 with R8: exact hazen percentile of rho over the leaf's P_1 */
+  double *sorted_rho = (double *)malloc(sizeof(double) * n1);
+  uint8_t *in2 = (uint8_t *)malloc(n1);
+  if (!sorted_rho || !in2) return ORC_ENOMEM;
+  memcpy(sorted_rho, rho, sizeof(double) * n1);
+  qsort(sorted_rho, n1, sizeof(double), cmp_double);
+  double pos = (double)n1 * (double)p->rho_percentile / 100.0 + 0.5;
+  double cc = ceil(pos);
+  uint32_t crank = (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;
+  double thr = sorted_rho[crank - 1];
+  uint32_t m2 = 0;
+  for (uint32_t a = 0; a < n1; ++a) {
+    in2[a] = rho[a] >= thr;
+    if (in2[a]) sorted_rho[m2++] = rho[a];
+    else c->stage_all[p1[a]] = 2;
+  }
+
+  /* Eq. 16 with R9: median of rho over P_2 */
+  qsort(sorted_rho, m2, sizeof(double), cmp_double);
+  double rho_med = (m2 & 1u) ? sorted_rho[(m2 - 1) / 2]
+                             : 0.5 * (sorted_rho[m2 / 2 - 1] + sorted_rho[m2 / 2]);
+  if (o->leaf_rho_med) o->leaf_rho_med[leaf_id] = rho_med;
+  if (o->leaf_n2) o->leaf_n2[leaf_id] = m2;
+
+  /* Eq. 15-21 with R10: dual-weight gravitational score */
+  const double alpha = p->alpha, sigma = p->sigma, gamma = p->gamma;
+  const double eps_rho = p->eps_rho, eps_k = p->eps_k;
+  const double wden_den = rho_med * rho_med + eps_rho;
+  ranked_t *rk = (ranked_t *)malloc(sizeof(ranked_t) * (m2 ? m2 : 1));
+  if (!rk) return ORC_ENOMEM;
+  uint32_t r = 0;
+  for (uint32_t a = 0; a < n1; ++a) {
+    if (!in2[a]) continue;
+    double F = 0.0, dA = 0.0, dS = 0.0, dG = 0.0;
+    const double r2i = (double)r2[a];
+    for (uint32_t s = 0; s < keff; ++s) {
+      uint32_t b = nb[(size_t)a * keff + s];
+      double d2 = (double)nd2[(size_t)a * keff + s];
+      double W = rho[a] * rho[b] / wden_den;                      /* Eq. 17 base */
+      double w_den = pow(W, alpha / 2.0);                         /* Eq. 17      */
+      double w_dis = exp(-d2 / (2.0 * (sigma * sigma) * r2i));    /* Eq. 18-19   */
+      double D = pow(d2, gamma / 2.0);
+      double kern = 1.0 / (D + eps_k);                            /* Eq. 20      */
+      double t = w_den * w_dis * kern;                            /* Eq. 15, 21  */
+      F += t;
+      if (c->dF) {
+        dA += t * 0.5 * log(W);
+        dS += t * d2 / (sigma * sigma * sigma * r2i);
+        if (d2 > 0.0) dG += -t * D * 0.5 * log(d2) / (D + eps_k);
+      }
+    }
+    c->F_all[p1[a]] = F;
+    if (c->dF) {
+      c->dF[3 * (size_t)p1[a] + 0] = dA;
+      c->dF[3 * (size_t)p1[a] + 1] = dS;
+      c->dF[3 * (size_t)p1[a] + 2] = dG;
+    }
+    rk[r].f = F;
+    rk[r].idx = p1[a];
+    rk[r].pos = a;
+    ++r;
+  }
+
+  /* R11: selection */
+  if (p->select_mode == 0) {
+    qsort(rk, m2, sizeof(ranked_t), cmp_ranked);
+    double want = ceil((double)p->lambda * (double)m2);
+    uint32_t keep = (want > (double)m2) ? m2 : (uint32_t)want;
+    for (uint32_t t = 0; t < m2; ++t) c->stage_all[rk[t].idx] = (t < keep) ? 0 : 3;
+  } else {
+    for (uint32_t t = 0; t < m2; ++t)
+      c->stage_all[rk[t].idx] = (log(rk[t].f) >= (double)p->tau) ? 0 : 3;
+  }
+
+  free(rk); free(sorted_rho); free(in2);
+  free(nb); free(nd2); free(r2); free(rho); free(cand);
+  free(idx); free(vox); free(cnt); free(p1);
+  return ORC_OK;
+}
+
+static int check_params(const orc_params *p) {
+  if (!p) return ORC_EINVAL;
+  if (p->k == 0 || p->k > 64) return ORC_EINVAL;
+  if (p->leaf_capacity == 0) return ORC_EINVAL;
+  if (p->max_depth > 21) return ORC_EINVAL;
+  if (!(p->beta > 0.0f) || !isfinite(p->beta)) return ORC_EINVAL;
+  if (!(p->rho_percentile >= 0.0f && p->rho_percentile <= 100.0f)) return ORC_EINVAL;
+  if (!(p->lambda > 0.0f && p->lambda <= 1.0f)) return ORC_EINVAL;
+  if (!(p->gamma > 0.0f) || !isfinite(p->gamma)) return ORC_EINVAL;
+  if (!(p->sigma > 0.0f) || !isfinite(p->sigma)) return ORC_EINVAL;
+  if (!isfinite(p->alpha) || !(p->eps_rho >= 0.0f) || !(p->eps_k >= 0.0f)) return ORC_EINVAL;
+  if (p->select_mode > 1) return ORC_EINVAL;
+  if (!(p->temperature > 0.0f)) return ORC_EINVAL;
+  return ORC_OK;
+}
+
+static int run(const float *xyz, int64_t n, const orc_params *p, orc_out *o, double *dF,
+               double *F_all, uint8_t *stage_all) {
+  int st = check_params(p);
+  if (st) return st;
+  for (int64_t i = 0; i < 3 * n; ++i)
+    if (!isfinite(xyz[i])) return ORC_ENONFINITE;
+  if (o->n_leaves) *o->n_leaves = 0;
+  if (n == 0) return ORC_OK;
+
+  /* R1: root cube */
+  float lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) { lo[a] = xyz[a]; hi[a] = xyz[a]; }
+  for (int64_t i = 1; i < n; ++i)
+    for (int a = 0; a < 3; ++a) {
+      float v = xyz[3 * i + a];
+      if (v < lo[a]) lo[a] = v;
+      if (v > hi[a]) hi[a] = v;
+    }
+  float side = 0.0f;
+  for (int a = 0; a < 3; ++a) {
+    float e = hi[a] - lo[a];
+    if (e > side) side = e;
+  }
+  if (side == 0.0f) side = 1.0f;
+  float s = 2097152.0f / side;
+  if (o->root) { o->root[0] = lo[0]; o->root[1] = lo[1]; o->root[2] = lo[2]; o->root[3] = side; }
+
+  keyed_t *sorted = (keyed_t *)malloc(sizeof(keyed_t) * (size_t)n);
+  leaf_t *leaves = (leaf_t *)malloc(sizeof(leaf_t) * (size_t)n);
+  if (!sorted || !leaves) return ORC_ENOMEM;
+  for (int64_t i = 0; i < n; ++i) {
+    uint32_t q[3];
+    for (int a = 0; a < 3; ++a) q[a] = quantise(xyz[3 * i + a], lo[a], s);
+    sorted[i].key = orc_interleave(q[0], q[1], q[2]);
+    sorted[i].idx = (uint32_t)i;
+    if (o->key) o->key[i] = sorted[i].key;
+  }
+  /* Sec. 3: sort by (key, index), then split top-down (R2) */
+  qsort(sorted, (size_t)n, sizeof(keyed_t), cmp_keyed);
+  octree_t tree = {sorted, p->leaf_capacity, p->max_depth, leaves, 0};
+  octree_build(&tree, 0, 0, (uint32_t)n);
+  if (o->n_leaves) *o->n_leaves = tree.n_leaves;
+
+  ctx_t c = {xyz, p, side * INV_TWO21, o, dF, F_all, stage_all};
+  for (int64_t i = 0; i < n; ++i) { F_all[i] = 0.0; stage_all[i] = 0; }
+  for (int64_t L = 0; L < tree.n_leaves; ++L) {
+    if (o->leaf_start) o->leaf_start[L] = leaves[L].start;
+    if (o->leaf_count) o->leaf_count[L] = leaves[L].count;
+    if (o->leaf_level) o->leaf_level[L] = leaves[L].level;
+    st = process_leaf(&c, sorted, &leaves[L], (uint32_t)L);
+    if (st) break;
+  }
+  /* Eq. 22: the union of the leaves' survivors, as a mask in input order */
+  for (int64_t i = 0; i < n; ++i) {
+    if (o->stage) o->stage[i] = stage_all[i];
+    if (o->mask) o->mask[i] = stage_all[i] == 0;
+    if (o->score) o->score[i] = F_all[i];
+  }
+  free(sorted);
+  free(leaves);
+  return st;
+}
+
+int orc_denoise(const float *xyz, int64_t n, const orc_params *p, orc_out *out) {
+  orc_out none;
+  memset(&none, 0, sizeof none);
+  if (!out) out = &none;
+  double *F = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  uint8_t *stg = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+  if (!F || !stg) return ORC_ENOMEM;
+  int st = run(xyz, n, p, out, NULL, F, stg);
+  free(F);
+  free(stg);
+  return st;
+}
+
+/* R12: soft-F1 of the differentiable form and its exact gradient */
+int orc_softf1(const float *xyz, int64_t n, const orc_params *p, const uint8_t *noise,
+               const uint8_t *in_loss, double *loss, double grad[4], double *removal) {
+  orc_out none;
+  memset(&none, 0, sizeof none);
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  double *F = (double *)malloc(sizeof(double) * nn);
+  double *dF = (double *)malloc(sizeof(double) * nn * 3);
+  double *rm = (double *)malloc(sizeof(double) * nn);
+  double *dm = (double *)malloc(sizeof(double) * nn);   /* m(1-m)/T on P_2 */
+  uint8_t *stg = (uint8_t *)malloc(nn);
+  if (!F || !dF || !rm || !dm || !stg) return ORC_ENOMEM;
+  orc_params q = *p;
+  q.select_mode = 1;
+  int st = run(xyz, n, &q, &none, dF, F, stg);
+  if (st) return st;
+  const double T = p->temperature, tau = p->tau;
+  double Sr = 0.0, Sy = 0.0, Sry = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    int scored = (stg[i] == 0 || stg[i] == 3);
+    double m = 0.0;
+    dm[i] = 0.0;
+    if (scored && F[i] > 0.0) {
+      double z = (log(F[i]) - tau) / T;
+      m = 1.0 / (1.0 + exp(-z));
+      dm[i] = m * (1.0 - m) / T;
+    }
+    rm[i] = 1.0 - m;
+    if (removal) removal[i] = rm[i];
+    if (in_loss && !in_loss[i]) continue;
+    Sr += rm[i];
+    Sy += (double)noise[i];
+    Sry += rm[i] * (double)noise[i];
+  }
+  double den = Sr + Sy;
+  *loss = (den > 0.0) ? 1.0 - 2.0 * Sry / den : 1.0;
+  double g[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = 0; i < n && den > 0.0; ++i) {
+    if (in_loss && !in_loss[i]) continue;
+    if (dm[i] == 0.0) continue;
+    /* d loss / d r_i */
+    double dl_dr = -2.0 * ((double)noise[i] * den - Sry) / (den * den);
+    /* r_i = 1 - sigmoid((ln F - tau)/T):  dr/dF = -m(1-m)/(T F), dr/dtau = m(1-m)/T */
+    double dr_dF = -dm[i] / F[i];
+    for (int k = 0; k < 3; ++k) g[k] += dl_dr * dr_dF * dF[3 * i + k];
+    g[3] += dl_dr * dm[i];
+  }
+  for (int k = 0; k < 4; ++k) grad[k] = g[k];
+  free(F); free(dF); free(rm); free(dm); free(stg);
+  return ORC_OK;
+}
