@@ -1,0 +1,434 @@
+"""Benchmark: points/s denoised on the dense-scan workload, one JSON line.
+
+Workload (default): one 560,000-point cloud (8 random superquadrics, 0.5 %
+surface jitter, 10 % uniform outliers, 2 % in 20 Gaussian blobs; seed 1),
+K = 32, leaf capacity 512, the plain per-frame path (denoise_run with device
+buffers).  A "step" denoises the whole cloud: bounding cube, Morton keys,
+radix sort, octree leaves, voxel gate, kNN + density gate, score, selection.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on
+the library's stream; between timed steps L2 is flushed by writing a 256 MiB
+buffer (outside the event pair).  Under torchrun each rank denoises its own
+cloud (seed 1 + rank): weak scaling, no collective on the data path; the
+reported time is the max over ranks.
+
+Extra objects on the line:
+  roofline      the fused leaf kernel (kNN + score), timed live with the
+                library's per-stage CUDA events; FP32 work = 8 flop per
+                candidate pair (3 sub + 1 mul + 2 fma of d^2)
+  e2e           the same metric through the public call with pinned HOST
+                buffers, copies included
+  cpu_baseline  the FP64 oracle on the machine's host cores, bounded sample
+  batched       64 LiDAR frames (60k-130k points) as one graph-captured batch,
+                against the same frames one call each
+``--impl reference`` times the FP64 oracle instead (the reference arm).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "points/s denoised; ms/frame p50/p99 batched vs plain GPU path at oracle mask"
+UNIT = "points/s"
+WORKLOAD = "dense_scan_560k_k32"
+FLOP_PER_PAIR = 8.0
+PROFILE = os.path.join(ROOT, "profiles", "leaf_kernel_dense_scan.txt")
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gd_leaf.cu", "gd_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2512_10386_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic():
+    """DRAM bytes per launch of the leaf kernel from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    if not os.path.exists(PROFILE):
+        return None
+    vals = {}
+    with open(PROFILE) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != _kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_workload"])
+    except (KeyError, ValueError):
+        return None
+
+
+def _workload(rank: int):
+    import synth
+    return synth.superquadric_scan(seed=1 + rank)
+
+
+def _oracle_crop(xyz, frac=0.125):
+    """A spatial crop of the cloud (its lowest-x fraction): the per-point work of
+    the method depends on local density, which a crop keeps."""
+    order = np.argsort(xyz[:, 0], kind="stable")
+    return np.ascontiguousarray(xyz[order[: int(len(xyz) * frac)]])
+
+
+def _oracle_params():
+    import oracle
+    from paper_2512_10386_gb300 import Params
+    p = Params(k=32)
+    return oracle.Params(k=p.k, leaf_capacity=p.leaf_capacity, max_depth=p.max_depth, beta=p.beta,
+                         min_vox_count=p.min_vox_count, rho_percentile=p.rho_percentile, lam=p.lam)
+
+
+def cpu_baseline_sample(xyz, target_s=15.0):
+    """The FP64 oracle, single-threaded, on a crop of the cloud, about target_s of work."""
+    import oracle
+    crop = _oracle_crop(xyz)
+    op = _oracle_params()
+    times = []
+    t_all = time.perf_counter()
+    while not times or (time.perf_counter() - t_all < target_s and len(times) < 5):
+        t0 = time.perf_counter()
+        oracle.denoise(crop, op)
+        times.append(time.perf_counter() - t0)
+    best = min(times)
+    return {"value": len(crop) / best, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(crop)} points (lowest-x 1/8 of the dense-scan cloud), {len(times)} runs, "
+                      f"best {best:.2f} s, single thread"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle as it stands, one crop of the workload per step."""
+    import oracle
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    xyz, _ = _workload(0)
+    crop = _oracle_crop(xyz)
+    op = _oracle_params()
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.denoise(crop, op)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = len(crop) * len(times) / sum(times)
+    sample = f"{len(crop)} points per step (lowest-x 1/8 of the dense-scan cloud), single thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+        __graft_entry__.build()
+    from paper_2512_10386_gb300 import Denoiser, Params
+
+    xyz_np, _ = _workload(rank)
+    n = len(xyz_np)
+    P = Params(k=32, leaf_capacity=512)
+    d = Denoiser(max_points=n, device=local)
+    stream = torch.cuda.Stream()
+    xyz = torch.from_numpy(xyz_np).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = d.run(xyz, P, stream=stream)
+    torch.cuda.synchronize()
+
+    d.set_profiling(True)
+    for _ in range(args.warmup):
+        d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms, leaf_ms = [], []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        for s in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(s))
+                ev[s][0].record(stream)
+            d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
+            ev[s][1].record(stream)
+            st = d.stats()
+            launches += st["launches"]
+            leaf_ms.append(st["stage_ms"][3])
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stats = d.stats()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = n * world * args.steps / (total_ms / 1000.0)
+
+    # ---- roofline of the fused leaf kernel (kNN + score)
+    peaks, peak_kind = _peaks()
+    props = torch.cuda.get_device_properties(local)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    leaf_avg_ms = sum(leaf_ms) / len(leaf_ms)
+    achieved = stats["knn_pairs"] * FLOP_PER_PAIR / (leaf_avg_ms / 1000.0) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak_tflops, "traffic": _profile_traffic(),
+                "kernel": "gd::k_leaf<32> (voxel gate + kNN + density gate + score + selection)",
+                "work": f"{stats['knn_pairs']} candidate pairs x {FLOP_PER_PAIR:g} FP32 flop per launch",
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:g} MHz "
+                              f"(max SM clock, {peak_kind} peaks file)",
+                "leaf_kernel_ms": leaf_avg_ms, "share_of_step": leaf_avg_ms / (total_ms / args.steps)}
+
+    # ---- end to end through the public call with pinned host buffers
+    d.set_profiling(False)
+    xyz_h = torch.from_numpy(xyz_np).pin_memory()
+    mh = torch.empty(n, dtype=torch.uint8).pin_memory()
+    sh = torch.empty(n, dtype=torch.float32).pin_memory()
+    gh = torch.empty(n, dtype=torch.uint8).pin_memory()
+    for _ in range(2):
+        d.run(xyz_h, P, mask=mh, score=sh, stage=gh, stream=stream)
+    e2e_ms = []
+    for s in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.fill_(float(s))
+        a.record(stream)
+        d.run(xyz_h, P, mask=mh, score=sh, stage=gh, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_total = sum(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e = {"value": n * world * args.steps / (e2e_total / 1000.0), "unit": UNIT,
+           "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 6 * n,
+           "ms_per_step": e2e_total / args.steps}
+
+    # ---- graph-captured replay of the same frame, and the batched workload
+    d.set_graphs(True)
+    d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
+    g_ms = []
+    for s in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.fill_(float(s))
+        a.record(stream)
+        d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        g_ms.append(a.elapsed_time(b))
+    d.set_graphs(False)
+    graph = {"value": n * args.steps / (sum(g_ms) / 1000.0), "unit": UNIT,
+             "ms_per_step": sum(g_ms) / args.steps}
+    d.close()
+
+    batched = None
+    if not args.no_batch:
+        batched = run_batched(args, stream, flush)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    cpu = cpu_baseline_sample(xyz_np) if (world == 1 and not args.no_cpu) else None
+    srt = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points_per_frame": n, "k": P.k, "leaf_capacity": P.leaf_capacity,
+                   "path": "plain per-frame denoise_run, device buffers, direct launches",
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "ms_per_frame": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+        "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "graph_replay": graph, "batched": batched,
+        "clocks": clocks.summary(), "gpu_launches": launches,
+        "stats": {k: stats[k] for k in ("n_leaves", "knn_pairs", "n_p1", "n_p2", "launches")},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_batched(args, stream, flush):
+    """64 LiDAR frames of 60k-130k points: one graph-captured batch vs one call per frame."""
+    import torch
+
+    import synth
+    from paper_2512_10386_gb300 import Denoiser, Params
+    frames = synth.lidar_batch(n_frames=args.frames)
+    sizes = [len(f[0]) for f in frames]
+    offs = np.cumsum([0] + sizes).tolist()
+    xyz = torch.from_numpy(np.concatenate([f[0] for f in frames])).cuda()
+    total = int(offs[-1])
+    P = Params(k=24)
+    d = Denoiser(max_points=total, max_frames=len(frames))
+    mask = torch.empty(total, dtype=torch.uint8, device="cuda")
+    score = torch.empty(total, dtype=torch.float32, device="cuda")
+    stage = torch.empty(total, dtype=torch.uint8, device="cuda")
+    # plain path: one call per frame
+    per_frame = []
+    for rep in range(args.warmup + max(1, args.steps // 4)):
+        for f in range(len(frames)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0, s1 = offs[f], offs[f + 1]
+            a.record(stream)
+            d.run(xyz[s0:s1], P, mask=mask[s0:s1], score=score[s0:s1], stage=stage[s0:s1], stream=stream)
+            b.record(stream)
+            if rep >= args.warmup:
+                per_frame.append((a, b))
+    torch.cuda.synchronize()
+    plain_ms = [a.elapsed_time(b) for a, b in per_frame]
+    plain_mask = mask.clone()
+    # batched path: one graph per batch
+    d.set_graphs(True)
+    d.run_batch(xyz, offs, P, mask=mask, score=score, stage=stage, stream=stream)
+    torch.cuda.synchronize()
+    identical = bool(torch.equal(mask, plain_mask))
+    batch_ms = []
+    for s in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.fill_(float(s))
+        a.record(stream)
+        d.run_batch(xyz, offs, P, mask=mask, score=score, stage=stage, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            batch_ms.append(a.elapsed_time(b))
+    d.close()
+    ps = sorted(plain_ms)
+    per_frame_batched = [m / len(frames) for m in batch_ms]
+    return {
+        "workload": f"{len(frames)} LiDAR frames, {min(sizes)}-{max(sizes)} points, {total} total, K=24",
+        "batched_points_per_s": total * len(batch_ms) / (sum(batch_ms) / 1000.0),
+        "plain_points_per_s": total * len(plain_ms) / len(frames) / (sum(plain_ms) / 1000.0),
+        "batched_ms_per_batch": sum(batch_ms) / len(batch_ms),
+        "batched_ms_per_frame": statistics.mean(per_frame_batched),
+        "plain_ms_per_frame": {"p50": ps[len(ps) // 2], "p99": ps[min(len(ps) - 1, int(0.99 * len(ps)))]},
+        "masks_identical": identical,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=64)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

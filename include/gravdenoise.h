@@ -1,0 +1,189 @@
+/*
+ * gravdenoise.h -- C ABI of the GB300 (sm_103a) adaptive dual-weight
+ * gravitational point-cloud denoiser (arXiv 2512.10386, Sec. 3).
+ *
+ * The problem statement (Sec. 3): given a cloud P = {p_1 .. p_N} of xyz
+ * points, partition it with an octree into leaves {P_t} (Eq. 10), remove
+ * isolated points with an adaptive voxel occupancy gate in each leaf
+ * (Eq. 11-12), remove low-density points with a kNN density percentile gate
+ * (Eq. 13-14), score the survivors with the density/distance dual-weight
+ * gravitational sum (Eq. 15-21), keep the best of each leaf and return the
+ * union of the leaves' survivors (Eq. 22).  Here the result is a per-point
+ * keep mask in input order, plus the scores and the stage that removed each
+ * point.
+ *
+ * Conventions shared by every call:
+ *  - Points are float32 xyz, array-of-structures [n][3] (12 bytes a point).
+ *  - Buffers may be host or device pointers; the library detects which
+ *    (cudaPointerGetAttributes).  Host buffers are staged through the
+ *    context's device memory with asynchronous copies on the given stream;
+ *    pinned host memory makes those copies truly asynchronous.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  All work
+ *    of a call is ordered on that stream.
+ *  - The caller owns every buffer it passes; the context owns all scratch.
+ *  - Calls on one context are not thread-safe: use one context per host
+ *    thread, or serialise.  Different contexts are independent.
+ *  - Return value: DENOISE_OK (0) or a negative DENOISE_E_* status.
+ */
+#ifndef GRAVDENOISE_H
+#define GRAVDENOISE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DENOISE_OK 0
+#define DENOISE_E_INVAL (-1)     /* bad argument or parameter                          */
+#define DENOISE_E_NONFINITE (-2) /* a coordinate is NaN or Inf (rejected, not filtered) */
+#define DENOISE_E_CAPACITY (-3)  /* more points or frames than the context was made for */
+#define DENOISE_E_NOMEM (-4)     /* device or pinned allocation failed                  */
+#define DENOISE_E_TIMEOUT (-5)   /* a bounded device-side wait ran out                  */
+#define DENOISE_E_CUDA (-6)      /* a CUDA runtime call failed                          */
+#define DENOISE_E_STATE (-7)     /* call out of order (e.g. backward without forward)   */
+
+/* Selection rule of the last step. */
+#define DENOISE_SELECT_TOPRATIO 0u  /* keep the best ceil(lambda*|P_2|) of each leaf (Sec. 3, end) */
+#define DENOISE_SELECT_THRESHOLD 1u /* keep ln F_i >= tau (differentiable form)                   */
+
+/*
+ * Method parameters.  Every field is read on every call.  Values the paper
+ * states are noted; the others are unstated there and are readings.
+ */
+typedef struct denoise_params {
+  uint32_t k;              /* K neighbours, 1..64 (paper default 12; Eq. 13, Sec. 4.3.1)        */
+  uint32_t leaf_capacity;  /* max points per octree leaf, >= 1 (Sec. 3)                         */
+  uint32_t max_depth;      /* octree depth limit 0..21, the minimum leaf side rule (Sec. 3)     */
+  float beta;              /* voxel enlargement coefficient > 0 (Eq. 11)                        */
+  uint32_t min_vox_count;  /* n_v, minimum voxel occupancy (Eq. 12; paper 4)                    */
+  float rho_percentile;    /* q in percent, 0..100, MATLAB prctile units (Eq. 14; paper 0.2)    */
+  float alpha;             /* density weighting index (Eq. 17)                                  */
+  float sigma;             /* distance-weight scale > 0, sigma_i = sigma * r_K,i (Eq. 18-19)    */
+  float gamma;             /* kernel exponent > 0: 1/((d^2)^(gamma/2) + eps_k); paper 2 (Eq. 20)*/
+  float eps_rho;           /* epsilon of Eq. 17, >= 0                                           */
+  float eps_k;             /* epsilon of Eq. 20, >= 0                                           */
+  uint32_t select_mode;    /* DENOISE_SELECT_TOPRATIO or DENOISE_SELECT_THRESHOLD               */
+  float lambda;            /* Top-lambda keep ratio in (0, 1] (Sec. 3, end)                     */
+  float tau;               /* log-score threshold of the THRESHOLD rule                         */
+  float temperature;       /* soft-mask temperature T > 0 (differentiable form only)            */
+} denoise_params;
+
+typedef struct denoise_ctx denoise_ctx;
+
+/*
+ * Create a context on CUDA device `device` able to process up to
+ * `max_points` points in one call, split into at most `max_frames` frames.
+ * All device scratch (sort buffers, octree leaf table, per-leaf spill space)
+ * is allocated here, sized for max_points; no later call allocates device
+ * memory.  *out receives the context (NULL on failure).
+ * Errors: E_INVAL (out NULL, max_points or max_frames 0), E_NOMEM, E_CUDA.
+ */
+int denoise_create(denoise_ctx **out, int device, size_t max_points, uint32_t max_frames);
+
+/* Release a context and all its memory.  NULL is a no-op.  Waits for the
+ * context's outstanding work first. */
+int denoise_destroy(denoise_ctx *ctx);
+
+/* Static English text for a status code. */
+const char *denoise_strerror(int status);
+
+/*
+ * Denoise one cloud (Sec. 3, Eq. 10-22).
+ *  xyz   [n][3] float32, host or device.
+ *  mask  [n] uint8, 1 = keep (the point belongs to P_denoise, Eq. 22); may be NULL.
+ *  score [n] float32, F_i (Eq. 21) for points of P_2, 0 otherwise; may be NULL.
+ *  stage [n] uint8: 0 kept, 1 removed by the voxel gate (Eq. 12), 2 removed
+ *        by the density gate (Eq. 14, or a leaf too small for a neighbour),
+ *        3 removed by the score selection; may be NULL.
+ * n = 0 is a valid no-op.  In synchronous mode (the default, see
+ * denoise_set_sync) the call returns after the results are in place and
+ * reports device-side errors (E_NONFINITE, E_TIMEOUT); in asynchronous mode
+ * it returns once the work is enqueued and denoise_get_status reports them.
+ * Errors: E_INVAL, E_NONFINITE, E_CAPACITY, E_TIMEOUT, E_CUDA.
+ */
+int denoise_run(denoise_ctx *ctx, const float *xyz, size_t n, const denoise_params *p,
+                uint8_t *mask, float *score, uint8_t *stage, void *stream);
+
+/*
+ * Denoise `nframes` independent clouds in one pass.  The clouds are
+ * concatenated in `xyz` ([offsets[nframes]][3]); frame f owns points
+ * offsets[f] .. offsets[f+1]-1.  `offsets` is a HOST array of nframes+1
+ * non-decreasing values starting at 0.  mask/score/stage follow the same
+ * concatenated layout.  Each frame is denoised exactly as denoise_run would
+ * denoise it alone.  With graphs enabled (denoise_set_graphs) the whole batch
+ * runs as one captured CUDA graph, re-captured only when the frame layout,
+ * the buffers or the parameters change.
+ * Errors: as denoise_run; E_CAPACITY if nframes > max_frames.
+ */
+int denoise_run_batch(denoise_ctx *ctx, const float *xyz, const uint64_t *offsets, uint32_t nframes,
+                      const denoise_params *p, uint8_t *mask, float *score, uint8_t *stage,
+                      void *stream);
+
+/* Execution options of a context. */
+int denoise_set_sync(denoise_ctx *ctx, int synchronous);   /* default 1                     */
+int denoise_set_graphs(denoise_ctx *ctx, int enable);      /* default 0 (direct launches)   */
+int denoise_set_profiling(denoise_ctx *ctx, int enable);   /* per-stage CUDA events, default 0 */
+
+/* Wait for the context's last call on `stream` and return its device-side
+ * status (DENOISE_OK, E_NONFINITE or E_TIMEOUT). */
+int denoise_get_status(denoise_ctx *ctx, void *stream);
+
+/* Statistics of the last completed call (valid after it finished). */
+typedef struct denoise_stats {
+  uint64_t n_points;     /* points processed                                          */
+  uint64_t n_leaves;     /* octree leaves                                             */
+  uint64_t knn_pairs;    /* sum over leaves of |P_1|(|P_1|-1): candidate pairs scanned */
+  uint64_t n_p1;         /* points that passed the voxel gate                         */
+  uint64_t n_p2;         /* points that passed the density gate                       */
+  uint32_t launches;     /* kernels launched by the call                              */
+  uint32_t n_stages;     /* entries valid in stage_ms                                 */
+  float stage_ms[8];     /* with profiling: init+bbox+keys, sort, leaves, leaf kernel, ... */
+} denoise_stats;
+
+int denoise_get_stats(denoise_ctx *ctx, denoise_stats *out);
+
+/*
+ * Per-stage intermediates for parity checks.  Every pointer may be NULL;
+ * all are DEVICE pointers, per point in input order unless noted.
+ */
+typedef struct denoise_debug {
+  uint64_t *key;         /* [n] 63-bit Morton key of the point (root cube of its frame)   */
+  uint32_t *leaf_start;  /* [n] sorted position (within the frame) of its leaf's first point */
+  uint32_t *leaf_count;  /* [n] N_t of its leaf                                            */
+  float *leaf_h;         /* [n] adaptive voxel size h of its leaf (Eq. 11)                 */
+  uint32_t *vox_count;   /* [n] occupancy of its voxel (Eq. 12)                            */
+  float *r2;             /* [n] floored squared distance to the k-th neighbour, P_1 only   */
+  uint32_t *nbr;         /* [n][k] neighbour indices (input order), 0xFFFFFFFF padding     */
+  float *nbr_d2;         /* [n][k] squared neighbour distances (FP32), 0 padding           */
+  double *leaf_rho_med;  /* [n] rho_med of its leaf (Eq. 16), 0 if the leaf scores nobody  */
+} denoise_debug;
+
+/* denoise_run with intermediates written to `dbg` (may be NULL). */
+int denoise_run_debug(denoise_ctx *ctx, const float *xyz, size_t n, const denoise_params *p,
+                      uint8_t *mask, float *score, uint8_t *stage, const denoise_debug *dbg,
+                      void *stream);
+
+/*
+ * Differentiable form (reading of Sec. 3 for calibration; the paper itself
+ * only thresholds).  With training enabled, the forward keeps, for every
+ * scored point, its neighbour list and density terms on the device.
+ *  denoise_soft_removal: removal probability r_i = 1 - sigmoid((ln F_i - tau)/T)
+ *    for points of P_2 and 1 for points removed by the gates, for the last
+ *    forward call and its parameters; removal [n] float32 (host or device).
+ *  denoise_backward: given dL/dr_i ([n] float32, host or device) for the last
+ *    forward call, accumulate dL/d(alpha, sigma, gamma, tau) into grad4
+ *    (HOST double[4], overwritten), with the neighbour sets, gates and
+ *    densities held fixed (none of them depends on these four parameters).
+ *    Reductions are in FP64 with a fixed order: results are deterministic.
+ * Errors: E_STATE if the last forward did not run with training enabled.
+ */
+int denoise_set_training(denoise_ctx *ctx, int enable);  /* default 0 */
+int denoise_soft_removal(denoise_ctx *ctx, float *removal, void *stream);
+int denoise_backward(denoise_ctx *ctx, const float *grad_removal, double *grad4, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRAVDENOISE_H */

@@ -1,0 +1,558 @@
+// gd_api.cu -- the C ABI declared in include/gravdenoise.h: contexts, argument
+// checks, host/device staging, kernel sequencing, optional CUDA-graph capture.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "gd_common.cuh"
+
+using namespace gd;
+
+struct denoise_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  size_t max_points = 0;
+  uint32_t max_frames = 0;
+  uint32_t max_tiles = 0;
+  // device memory
+  float *d_xyz = nullptr;
+  uint8_t *d_mask = nullptr;
+  float *d_score = nullptr;
+  uint8_t *d_stage = nullptr;
+  float *d_gin = nullptr;
+  unsigned long long *d_keys[2] = {nullptr, nullptr};
+  uint32_t *d_vals[2] = {nullptr, nullptr};
+  float4 *d_spts = nullptr;
+  FrameInfo *d_frames = nullptr;
+  Tile *d_tiles = nullptr;
+  uint32_t *d_hist = nullptr;
+  uint32_t *d_base = nullptr;
+  uint32_t *d_lookback = nullptr;
+  Leaf *d_leaves = nullptr;
+  Counters *d_ctr = nullptr;
+  unsigned char *d_big = nullptr;
+  uint32_t big_bpp = 0;
+  double *d_partials = nullptr;
+  double *d_grad = nullptr;
+  // training cache (allocated by denoise_set_training)
+  TrainCache train{};
+  bool train_alloc = false;
+  // pinned host memory
+  Tile *h_tiles = nullptr;
+  FrameInfo *h_frames = nullptr;
+  Counters *h_ctr = nullptr;
+  double *h_grad = nullptr;
+  // options
+  int sync = 1, graphs = 0, profiling = 0, training = 0;
+  // last call
+  size_t last_n = 0;
+  uint32_t last_nframes = 0;
+  denoise_params last_p{};
+  bool last_trained = false;
+  int last_launches = 0;
+  int last_status_read = 0;
+  float stage_ms[8] = {0};
+  int n_stage_ms = 0;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // graph cache (captured on a private stream, launched on the caller's)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<unsigned char> gkey;
+  // frame layout cache
+  std::vector<uint64_t> layout;
+  uint32_t ntiles = 0;
+};
+
+namespace {
+
+constexpr size_t kBackPartials = 1024;
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int check_params(const denoise_params *p) {
+  if (!p) return DENOISE_E_INVAL;
+  if (p->k == 0 || p->k > 64) return DENOISE_E_INVAL;
+  if (p->leaf_capacity == 0) return DENOISE_E_INVAL;
+  if (p->max_depth > 21) return DENOISE_E_INVAL;
+  if (!(p->beta > 0.0f) || !isfinite(p->beta)) return DENOISE_E_INVAL;
+  if (!(p->rho_percentile >= 0.0f && p->rho_percentile <= 100.0f)) return DENOISE_E_INVAL;
+  if (!(p->lambda > 0.0f && p->lambda <= 1.0f)) return DENOISE_E_INVAL;
+  if (!(p->gamma > 0.0f) || !isfinite(p->gamma)) return DENOISE_E_INVAL;
+  if (!(p->sigma > 0.0f) || !isfinite(p->sigma)) return DENOISE_E_INVAL;
+  if (!isfinite(p->alpha) || !(p->eps_rho >= 0.0f) || !(p->eps_k >= 0.0f)) return DENOISE_E_INVAL;
+  if (!isfinite(p->eps_rho) || !isfinite(p->eps_k) || !isfinite(p->tau)) return DENOISE_E_INVAL;
+  if (p->select_mode > 1) return DENOISE_E_INVAL;
+  if (!(p->temperature > 0.0f) || !isfinite(p->temperature)) return DENOISE_E_INVAL;
+  return DENOISE_OK;
+}
+
+template <typename T>
+int dalloc(T **p, size_t count) {
+  if (count == 0) count = 1;
+  return cudaMalloc((void **)p, sizeof(T) * count) == cudaSuccess ? 0 : -1;
+}
+
+void free_ctx(denoise_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  void *dptrs[] = {c->d_xyz, c->d_mask, c->d_score, c->d_stage, c->d_gin, c->d_keys[0], c->d_keys[1],
+                   c->d_vals[0], c->d_vals[1], c->d_spts, c->d_frames, c->d_tiles, c->d_hist, c->d_base,
+                   c->d_lookback, c->d_leaves, c->d_ctr, c->d_big, c->d_partials, c->d_grad,
+                   c->train.nbr, c->train.nd2, c->train.ell, c->train.r2, c->train.F, c->train.stage};
+  for (void *p : dptrs)
+    if (p) cudaFree(p);
+  void *hptrs[] = {c->h_tiles, c->h_frames, c->h_ctr, c->h_grad};
+  for (void *p : hptrs)
+    if (p) cudaFreeHost(p);
+  for (auto &e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  cudaGetLastError();
+  delete c;
+}
+
+// A failed runtime call leaves a "last error" in the process-wide runtime that
+// the next caller (e.g. PyTorch) would report as its own: clear it here.
+int cuda_fail() {
+  cudaGetLastError();
+  return DENOISE_E_CUDA;
+}
+
+int map_status(uint32_t st) {
+  if (st & kStNonFinite) return DENOISE_E_NONFINITE;
+  if (st & kStTimeout) return DENOISE_E_TIMEOUT;
+  if (st & kStInternal) return DENOISE_E_CUDA;
+  return DENOISE_OK;
+}
+
+// Front-end tiles of a frame layout (host); returns the tile count.
+uint32_t build_tiles(denoise_ctx *c, const uint64_t *offsets, uint32_t nframes) {
+  uint32_t nt = 0;
+  for (uint32_t f = 0; f < nframes; ++f) {
+    const uint32_t b = (uint32_t)offsets[f], e = (uint32_t)offsets[f + 1];
+    c->h_frames[f] = FrameInfo{};
+    c->h_frames[f].begin = b;
+    c->h_frames[f].end = e;
+    const uint32_t first = nt;
+    for (uint32_t s = b; s < e; s += kTilePts) {
+      const uint32_t te = (e - s > (uint32_t)kTilePts) ? s + kTilePts : e;
+      c->h_tiles[nt++] = Tile{f, s, te, first};
+    }
+  }
+  return nt;
+}
+
+// Enqueue one whole call on `st`.  Returns a DENOISE status (host-side errors only).
+int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, const denoise_params &p,
+            uint8_t *mask, float *score, uint8_t *stage, const denoise_debug *dbg, bool use_events,
+            cudaStream_t st, const float *xyz_host, uint8_t *mask_h, float *score_h, uint8_t *stage_h) {
+  int launches = 0;
+  if (xyz_host) {
+    if (cudaMemcpyAsync(c->d_xyz, xyz_host, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+      return cuda_fail();
+  }
+  cudaMemcpyAsync(c->d_tiles, c->h_tiles, sizeof(Tile) * c->ntiles, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(c->d_frames, c->h_frames, sizeof(FrameInfo) * nframes, cudaMemcpyHostToDevice, st);
+  if (use_events) cudaEventRecord(c->ev[0], st);
+  FrontArgs fa{};
+  fa.xyz = xyz_dev;
+  fa.n = n;
+  fa.frames = c->d_frames;
+  fa.nframes = nframes;
+  fa.tiles = c->d_tiles;
+  fa.ntiles = c->ntiles;
+  fa.keys[0] = c->d_keys[0];
+  fa.keys[1] = c->d_keys[1];
+  fa.vals[0] = c->d_vals[0];
+  fa.vals[1] = c->d_vals[1];
+  fa.spts = c->d_spts;
+  fa.digit_hist = c->d_hist;
+  fa.digit_base = c->d_base;
+  fa.lookback = c->d_lookback;
+  fa.leaves = c->d_leaves;
+  fa.ctr = c->d_ctr;
+  fa.dbg_key = dbg ? dbg->key : nullptr;
+  fa.max_depth = (int)p.max_depth;
+  fa.leaf_capacity = p.leaf_capacity;
+  if (launch_front(fa, st, &launches, use_events ? &c->ev[1] : nullptr, use_events ? &c->ev[2] : nullptr))
+    return cuda_fail();
+  if (use_events) cudaEventRecord(c->ev[3], st);
+  LeafArgs la{};
+  la.n = n;
+  la.spts = c->d_spts;
+  la.leaves = c->d_leaves;
+  la.frames = c->d_frames;
+  la.ctr = c->d_ctr;
+  la.p = p;
+  la.mask = mask;
+  la.score = score;
+  la.stage = stage;
+  if (dbg) {
+    la.dbg = *dbg;
+    la.use_dbg = 1;
+  }
+  la.big_scratch = c->d_big;
+  la.big_bpp = c->big_bpp;
+  const int kmax = leaf_kmax(p.k);
+  la.lmax = leaf_pick_lmax(p.leaf_capacity, kmax, c->smem_optin - 2048);
+  if (c->training) {
+    la.train = c->train;
+    la.train.k = p.k;
+    la.use_train = 1;
+  }
+  if (launch_leaf(la, c->num_sms, st)) return cuda_fail();
+  ++launches;
+  if (use_events) cudaEventRecord(c->ev[4], st);
+  if (mask_h) cudaMemcpyAsync(mask_h, c->d_mask, n, cudaMemcpyDeviceToHost, st);
+  if (score_h) cudaMemcpyAsync(score_h, c->d_score, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (stage_h) cudaMemcpyAsync(stage_h, c->d_stage, n, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+  c->last_launches = launches;
+  return cudaGetLastError() == cudaSuccess ? DENOISE_OK : DENOISE_E_CUDA;
+}
+
+int finish(denoise_ctx *c, cudaStream_t st, bool events) {
+  if (!c->sync) return DENOISE_OK;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_fail();
+  if (events) {
+    c->n_stage_ms = 4;
+    for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&c->stage_ms[i], c->ev[i], c->ev[i + 1]);
+  }
+  return map_status(c->h_ctr->status);
+}
+
+int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t nframes, const denoise_params *p,
+             uint8_t *mask, float *score, uint8_t *stage, const denoise_debug *dbg, void *stream) {
+  if (!c || !offsets) return DENOISE_E_INVAL;
+  int s = check_params(p);
+  if (s) return s;
+  if (nframes == 0) return DENOISE_E_INVAL;
+  if (nframes > c->max_frames) return DENOISE_E_CAPACITY;
+  if (offsets[0] != 0) return DENOISE_E_INVAL;
+  for (uint32_t f = 0; f < nframes; ++f)
+    if (offsets[f + 1] < offsets[f]) return DENOISE_E_INVAL;
+  const uint64_t n64 = offsets[nframes];
+  if (n64 > c->max_points) return DENOISE_E_CAPACITY;
+  if (cudaSetDevice(c->device) != cudaSuccess) return DENOISE_E_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_n = (size_t)n64;
+  c->last_nframes = nframes;
+  c->last_p = *p;
+  c->last_trained = false;
+  if (n64 == 0) {
+    memset(c->h_ctr, 0, sizeof(Counters));
+    c->last_launches = 0;
+    return DENOISE_OK;
+  }
+  if (!xyz) return DENOISE_E_INVAL;
+  const uint32_t n = (uint32_t)n64;
+  if (c->training && !c->train_alloc) return DENOISE_E_STATE;
+  if (c->training && p->k > 64) return DENOISE_E_INVAL;
+
+  // resolve host / device buffers
+  const bool xyz_dev = is_device_ptr(xyz);
+  const float *xyz_d = xyz_dev ? xyz : c->d_xyz;
+  const float *xyz_h = xyz_dev ? nullptr : xyz;
+  uint8_t *mask_d = mask, *mask_h = nullptr;
+  float *score_d = score, *score_h = nullptr;
+  uint8_t *stage_d = stage, *stage_h = nullptr;
+  if (mask && !is_device_ptr(mask)) { mask_h = mask; mask_d = c->d_mask; }
+  if (score && !is_device_ptr(score)) { score_h = score; score_d = c->d_score; }
+  if (stage && !is_device_ptr(stage)) { stage_h = stage; stage_d = c->d_stage; }
+
+  // frame layout -> tiles (re-built only when it changes)
+  bool layout_changed = c->layout.size() != nframes + 1 ||
+                        memcmp(c->layout.data(), offsets, sizeof(uint64_t) * (nframes + 1)) != 0;
+  if (layout_changed) {
+    if (c->gexec) cudaStreamSynchronize(st);  // the pinned tables may be read by a graph in flight
+    c->layout.assign(offsets, offsets + nframes + 1);
+    c->ntiles = build_tiles(c, offsets, nframes);
+  }
+  const bool events = c->profiling && !c->graphs && c->sync;
+  int rc;
+  if (c->graphs && !dbg) {
+    // graph key: everything the captured work depends on
+    std::vector<unsigned char> key;
+    auto put = [&](const void *v, size_t b) {
+      const unsigned char *q = (const unsigned char *)v;
+      key.insert(key.end(), q, q + b);
+    };
+    put(p, sizeof(*p));
+    put(&xyz, sizeof(xyz));
+    put(&mask, sizeof(mask));
+    put(&score, sizeof(score));
+    put(&stage, sizeof(stage));
+    put(&c->training, sizeof(c->training));
+    put(offsets, sizeof(uint64_t) * (nframes + 1));
+    if (!c->gexec || key != c->gkey) {
+      if (c->gexec) {
+        cudaStreamSynchronize(st);
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+      }
+      if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_fail();
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_fail();
+      rc = enqueue(c, xyz_d, n, nframes, *p, mask_d, score_d, stage_d, nullptr, false, c->cap_stream, xyz_h, mask_h,
+                   score_h, stage_h);
+      const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+      if (rc || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc ? rc : DENOISE_E_CUDA;
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&c->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_fail();
+      }
+      c->gkey.swap(key);
+    }
+    if (cudaGraphLaunch(c->gexec, st) != cudaSuccess) return cuda_fail();
+  } else {
+    rc = enqueue(c, xyz_d, n, nframes, *p, mask_d, score_d, stage_d, dbg, events, st, xyz_h, mask_h, score_h,
+                 stage_h);
+    if (rc) return rc;
+  }
+  c->last_trained = c->training != 0;
+  c->last_status_read = 0;
+  return finish(c, st, events);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *denoise_strerror(int s) {
+  switch (s) {
+    case DENOISE_OK: return "ok";
+    case DENOISE_E_INVAL: return "invalid argument or parameter";
+    case DENOISE_E_NONFINITE: return "input contains a NaN or infinite coordinate";
+    case DENOISE_E_CAPACITY: return "more points or frames than the context was created for";
+    case DENOISE_E_NOMEM: return "out of device or pinned host memory";
+    case DENOISE_E_TIMEOUT: return "a bounded device-side wait ran out";
+    case DENOISE_E_CUDA: return "CUDA runtime error";
+    case DENOISE_E_STATE: return "call out of order (no training forward to differentiate)";
+    default: return "unknown status";
+  }
+}
+
+int denoise_create(denoise_ctx **out, int device, size_t max_points, uint32_t max_frames) {
+  if (!out) return DENOISE_E_INVAL;
+  *out = nullptr;
+  if (max_points == 0 || max_frames == 0 || max_points >= (1u << 30)) return DENOISE_E_INVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return DENOISE_E_CUDA;
+  denoise_ctx *c = new (std::nothrow) denoise_ctx();
+  if (!c) return DENOISE_E_NOMEM;
+  c->device = device;
+  c->max_points = max_points;
+  c->max_frames = max_frames;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    free_ctx(c);
+    return DENOISE_E_CUDA;
+  }
+  c->num_sms = prop.multiProcessorCount;
+  c->smem_optin = prop.sharedMemPerBlockOptin;
+  c->max_tiles = (uint32_t)(max_points / kTilePts) + max_frames + 1;
+  c->big_bpp = leaf_big_bpp(64);
+  const size_t N = max_points;
+  int e = 0;
+  e |= dalloc(&c->d_xyz, 3 * N);
+  e |= dalloc(&c->d_mask, N);
+  e |= dalloc(&c->d_score, N);
+  e |= dalloc(&c->d_stage, N);
+  e |= dalloc(&c->d_gin, N);
+  e |= dalloc(&c->d_keys[0], N);
+  e |= dalloc(&c->d_keys[1], N);
+  e |= dalloc(&c->d_vals[0], N);
+  e |= dalloc(&c->d_vals[1], N);
+  e |= dalloc(&c->d_spts, N);
+  e |= dalloc(&c->d_frames, max_frames);
+  e |= dalloc(&c->d_tiles, c->max_tiles);
+  e |= dalloc(&c->d_hist, (size_t)max_frames * kMaxPasses * 256);
+  e |= dalloc(&c->d_base, (size_t)max_frames * kMaxPasses * 256);
+  e |= dalloc(&c->d_lookback, (size_t)kMaxPasses * c->max_tiles * 256);
+  e |= dalloc(&c->d_leaves, N);
+  e |= dalloc(&c->d_ctr, 1);
+  e |= dalloc(&c->d_big, N * c->big_bpp);
+  e |= dalloc(&c->d_partials, kBackPartials * 4);
+  e |= dalloc(&c->d_grad, 4);
+  if (e) {
+    cudaGetLastError();
+    free_ctx(c);
+    return DENOISE_E_NOMEM;
+  }
+  if (cudaMallocHost((void **)&c->h_tiles, sizeof(Tile) * c->max_tiles) != cudaSuccess ||
+      cudaMallocHost((void **)&c->h_frames, sizeof(FrameInfo) * max_frames) != cudaSuccess ||
+      cudaMallocHost((void **)&c->h_ctr, sizeof(Counters)) != cudaSuccess ||
+      cudaMallocHost((void **)&c->h_grad, sizeof(double) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    free_ctx(c);
+    return DENOISE_E_NOMEM;
+  }
+  memset(c->h_ctr, 0, sizeof(Counters));
+  for (auto &ev : c->ev) {
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      free_ctx(c);
+      return DENOISE_E_CUDA;
+    }
+  }
+  *out = c;
+  return DENOISE_OK;
+}
+
+int denoise_destroy(denoise_ctx *ctx) {
+  if (!ctx) return DENOISE_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  free_ctx(ctx);
+  return DENOISE_OK;
+}
+
+int denoise_run(denoise_ctx *ctx, const float *xyz, size_t n, const denoise_params *p, uint8_t *mask, float *score,
+                uint8_t *stage, void *stream) {
+  const uint64_t off[2] = {0, (uint64_t)n};
+  return run_impl(ctx, xyz, off, 1, p, mask, score, stage, nullptr, stream);
+}
+
+int denoise_run_debug(denoise_ctx *ctx, const float *xyz, size_t n, const denoise_params *p, uint8_t *mask,
+                      float *score, uint8_t *stage, const denoise_debug *dbg, void *stream) {
+  const uint64_t off[2] = {0, (uint64_t)n};
+  return run_impl(ctx, xyz, off, 1, p, mask, score, stage, dbg, stream);
+}
+
+int denoise_run_batch(denoise_ctx *ctx, const float *xyz, const uint64_t *offsets, uint32_t nframes,
+                      const denoise_params *p, uint8_t *mask, float *score, uint8_t *stage, void *stream) {
+  return run_impl(ctx, xyz, offsets, nframes, p, mask, score, stage, nullptr, stream);
+}
+
+int denoise_set_sync(denoise_ctx *ctx, int synchronous) {
+  if (!ctx) return DENOISE_E_INVAL;
+  ctx->sync = synchronous ? 1 : 0;
+  return DENOISE_OK;
+}
+
+int denoise_set_graphs(denoise_ctx *ctx, int enable) {
+  if (!ctx) return DENOISE_E_INVAL;
+  ctx->graphs = enable ? 1 : 0;
+  return DENOISE_OK;
+}
+
+int denoise_set_profiling(denoise_ctx *ctx, int enable) {
+  if (!ctx) return DENOISE_E_INVAL;
+  ctx->profiling = enable ? 1 : 0;
+  return DENOISE_OK;
+}
+
+int denoise_get_status(denoise_ctx *ctx, void *stream) {
+  if (!ctx) return DENOISE_E_INVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DENOISE_E_CUDA;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return DENOISE_E_CUDA;
+  return map_status(ctx->h_ctr->status);
+}
+
+int denoise_get_stats(denoise_ctx *ctx, denoise_stats *out) {
+  if (!ctx || !out) return DENOISE_E_INVAL;
+  memset(out, 0, sizeof(*out));
+  out->n_points = ctx->last_n;
+  out->n_leaves = ctx->h_ctr->n_leaves;
+  out->knn_pairs = ctx->h_ctr->knn_pairs;
+  out->n_p1 = ctx->h_ctr->n_p1;
+  out->n_p2 = ctx->h_ctr->n_p2;
+  out->launches = (uint32_t)ctx->last_launches;
+  out->n_stages = (uint32_t)ctx->n_stage_ms;
+  for (int i = 0; i < ctx->n_stage_ms && i < 8; ++i) out->stage_ms[i] = ctx->stage_ms[i];
+  return DENOISE_OK;
+}
+
+int denoise_set_training(denoise_ctx *ctx, int enable) {
+  if (!ctx) return DENOISE_E_INVAL;
+  if (enable && !ctx->train_alloc) {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return DENOISE_E_CUDA;
+    const size_t N = ctx->max_points;
+    int e = 0;
+    e |= dalloc(&ctx->train.nbr, N * 64);
+    e |= dalloc(&ctx->train.nd2, N * 64);
+    e |= dalloc(&ctx->train.ell, N);
+    e |= dalloc(&ctx->train.r2, N);
+    e |= dalloc(&ctx->train.F, N);
+    e |= dalloc(&ctx->train.stage, N);
+    if (e) {
+      cudaGetLastError();
+      return DENOISE_E_NOMEM;
+    }
+    ctx->train_alloc = true;
+  }
+  ctx->training = enable ? 1 : 0;
+  return DENOISE_OK;
+}
+
+int denoise_soft_removal(denoise_ctx *ctx, float *removal, void *stream) {
+  if (!ctx || !removal) return DENOISE_E_INVAL;
+  if (!ctx->last_trained) return DENOISE_E_STATE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DENOISE_E_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev = is_device_ptr(removal);
+  BackArgs a{};
+  a.train = ctx->train;
+  a.train.k = ctx->last_p.k;
+  a.n = (uint32_t)ctx->last_n;
+  a.p = ctx->last_p;
+  a.removal = dev ? removal : ctx->d_score;
+  if (a.n == 0) return DENOISE_OK;
+  if (launch_soft_removal(a, st)) return DENOISE_E_CUDA;
+  if (!dev) {
+    cudaMemcpyAsync(removal, ctx->d_score, sizeof(float) * a.n, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return DENOISE_E_CUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? DENOISE_OK : DENOISE_E_CUDA;
+}
+
+int denoise_backward(denoise_ctx *ctx, const float *grad_removal, double *grad4, void *stream) {
+  if (!ctx || !grad_removal || !grad4) return DENOISE_E_INVAL;
+  if (!ctx->last_trained) return DENOISE_E_STATE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DENOISE_E_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  BackArgs a{};
+  a.train = ctx->train;
+  a.train.k = ctx->last_p.k;
+  a.n = (uint32_t)ctx->last_n;
+  a.p = ctx->last_p;
+  if (a.n == 0) {
+    for (int i = 0; i < 4; ++i) grad4[i] = 0.0;
+    return DENOISE_OK;
+  }
+  const float *g = grad_removal;
+  if (!is_device_ptr(grad_removal)) {
+    cudaMemcpyAsync(ctx->d_gin, grad_removal, sizeof(float) * a.n, cudaMemcpyHostToDevice, st);
+    g = ctx->d_gin;
+  }
+  a.grad_r = g;
+  a.partials = ctx->d_partials;
+  a.grad4 = ctx->d_grad;
+  int launches = 0;
+  if (launch_backward(a, st, &launches)) return DENOISE_E_CUDA;
+  cudaMemcpyAsync(ctx->h_grad, ctx->d_grad, sizeof(double) * 4, cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return DENOISE_E_CUDA;
+  for (int i = 0; i < 4; ++i) grad4[i] = ctx->h_grad[i];
+  return DENOISE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// gd_common.cuh -- device-side types and helpers shared by the library's kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gravdenoise.h"
+
+namespace gd {
+
+constexpr uint32_t kQMax = 2097151u;                  // 2^21 - 1: 21-bit cell index per axis
+constexpr float kInvTwo21 = 4.76837158203125e-07f;    // 2^-21
+constexpr int kTilePts = 2048;                        // points per front-end tile
+constexpr int kFrontThreads = 256;
+constexpr int kFrontItems = kTilePts / kFrontThreads; // 8
+constexpr int kMaxPasses = 8;                         // 8-bit radix digits over <= 63 key bits
+constexpr uint32_t kSpinLimit = 1u << 22;             // bounded device-side waits
+
+// device status word bits
+enum : uint32_t {
+  kStNonFinite = 1u,
+  kStTimeout = 2u,
+  kStInternal = 4u,  // a bounds or consistency check failed; results are void
+};
+constexpr uint32_t kStFatal = kStNonFinite | kStTimeout | kStInternal;
+
+// One frame of a batch: its point range and root cube (filled on the device).
+struct FrameInfo {
+  uint32_t begin, end;
+  uint32_t lo_ord[3], hi_ord[3];  // order-preserving integer images of min / max (atomics)
+  float lo[3];
+  float side, s, delta;
+};
+
+// Front-end work tile: [begin, end) of one frame, <= kTilePts points.
+struct Tile {
+  uint32_t frame, begin, end, first_tile;  // first_tile: index of the frame's first tile
+};
+
+// Octree leaf.
+struct Leaf {
+  uint32_t start, count, frame, level;
+};
+
+struct Counters {
+  uint32_t status;
+  uint32_t n_leaves;
+  uint32_t leaf_work;                    // persistent leaf-kernel work counter
+  uint32_t tile_work[kMaxPasses];        // radix-pass tile counters
+  uint32_t pad;
+  unsigned long long knn_pairs;
+  unsigned long long n_p1;
+  unsigned long long n_p2;
+};
+
+// Train-mode cache written by the forward for the backward.
+struct TrainCache {
+  uint32_t *nbr;    // [n][k] neighbour global indices (P_1 points), 0xFFFFFFFF pad
+  float *nd2;       // [n][k] squared neighbour distances (FP32), 0 pad
+  float *ell;       // [n] log2(rho_i / sqrt(rho_med^2 + eps_rho)) for P_1 points
+  float *r2;        // [n] floored r_K^2 for P_1 points
+  float *F;         // [n] score (P_2), 0 otherwise
+  uint8_t *stage;   // [n]
+  uint32_t k;
+};
+
+__device__ __forceinline__ uint32_t f2ord(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {  // global memory only
+  uint32_t v;
+  asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// FP32 quantisation of one coordinate to a 21-bit cell: min(2^21-1, floor((x - lo) * s)).
+__device__ __forceinline__ uint32_t quantise(float x, float lo, float s) {
+  float f = floorf(__fmul_rn(__fsub_rn(x, lo), s));
+  return (f < 2097151.0f) ? (uint32_t)f : kQMax;
+}
+
+// Morton interleave: bit 3b+2 <- x_b, 3b+1 <- y_b, 3b <- z_b.
+__device__ __forceinline__ unsigned long long spread3(uint32_t v) {
+  unsigned long long x = v & 0x1FFFFFu;
+  x = (x | (x << 32)) & 0x1F00000000FFFFull;
+  x = (x | (x << 16)) & 0x1F0000FF0000FFull;
+  x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+  x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+__device__ __forceinline__ unsigned long long morton3(uint32_t qx, uint32_t qy, uint32_t qz) {
+  return (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+}
+
+// Host-side launch helpers (defined in gd_front.cu / gd_leaf.cu).
+struct FrontArgs {
+  const float *xyz;
+  uint32_t n;
+  FrameInfo *frames;
+  uint32_t nframes;
+  const Tile *tiles;
+  uint32_t ntiles;
+  unsigned long long *keys[2];
+  uint32_t *vals[2];
+  float4 *spts;
+  uint32_t *digit_hist;   // [nframes][kMaxPasses][256]
+  uint32_t *digit_base;   // [nframes][kMaxPasses][256]
+  uint32_t *lookback;     // [kMaxPasses][ntiles][256]
+  Leaf *leaves;
+  Counters *ctr;
+  uint64_t *dbg_key;
+  int max_depth;
+  uint32_t leaf_capacity;
+};
+
+int front_passes(int max_depth);
+int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t *ev_after_keys,
+                 cudaEvent_t *ev_after_sort);
+
+struct LeafArgs {
+  uint32_t n;                   // total points (bounds check of every output index)
+  const float4 *spts;
+  const Leaf *leaves;
+  const FrameInfo *frames;
+  Counters *ctr;
+  denoise_params p;
+  uint8_t *mask;
+  float *score;
+  uint8_t *stage;
+  denoise_debug dbg;
+  int use_dbg;
+  unsigned char *big_scratch;   // per-point spill space for leaves larger than the smem path
+  uint32_t big_bpp;             // bytes per point of big_scratch
+  uint32_t lmax;                // largest leaf handled in shared memory (power of two)
+  TrainCache train;
+  int use_train;
+};
+
+int leaf_kmax(uint32_t k);
+size_t leaf_smem_bytes(uint32_t lmax, int kmax);
+uint32_t leaf_big_bpp(int kmax);
+uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit);
+int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st);
+
+struct BackArgs {
+  TrainCache train;
+  uint32_t n;
+  denoise_params p;
+  const float *grad_r;   // [n] dL/dr_i
+  float *removal;        // [n] soft removal output
+  double *partials;      // [blocks][4]
+  double *grad4;         // [4]
+};
+int launch_soft_removal(const BackArgs &a, cudaStream_t st);
+int launch_backward(const BackArgs &a, cudaStream_t st, int *launches);
+
+}  // namespace gd

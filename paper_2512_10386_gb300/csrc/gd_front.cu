@@ -1,0 +1,434 @@
+// gd_front.cu -- front end of the path: root cube (Eq. 2 extents of each frame),
+// 63-bit Morton keys, a segmented LSD radix sort by key (octree order, Sec. 3),
+// and the octree leaf finder (leaf = shallowest node holding <= leaf_capacity
+// points, or a node at max_depth).
+//
+// Radix sort design (one kernel per 8-bit digit pass): a tile of 2,048 keys is
+// ranked stably inside the block with warp match_any, per-digit tile counts are
+// published to a look-back array and each tile's exclusive prefix is built by
+// decoupled look-back over earlier tiles of the same frame (bounded spins), on
+// top of per-frame digit bases taken from one upfront histogram kernel.  The
+// frame-major tile layout makes the sort segmented: frames never mix.
+#include "gd_common.cuh"
+
+namespace gd {
+
+// ---------------------------------------------------------------------------
+// init: reset counters, bbox accumulators and look-back flags
+// ---------------------------------------------------------------------------
+__global__ void k_init(FrameInfo *frames, uint32_t nframes, Counters *ctr, uint32_t *digit_hist,
+                       uint32_t *lookback, uint32_t n_lookback, int passes) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  if (tid == 0) {
+    ctr->status = 0;
+    ctr->n_leaves = 0;
+    ctr->leaf_work = 0;
+    for (int i = 0; i < kMaxPasses; ++i) ctr->tile_work[i] = 0;
+    ctr->knn_pairs = 0;
+    ctr->n_p1 = 0;
+    ctr->n_p2 = 0;
+  }
+  for (uint32_t f = tid; f < nframes; f += stride) {
+    for (int a = 0; a < 3; ++a) {
+      frames[f].lo_ord[a] = 0xFFFFFFFFu;
+      frames[f].hi_ord[a] = 0u;
+    }
+  }
+  const uint32_t nh = nframes * kMaxPasses * 256u;
+  for (uint32_t i = tid; i < nh; i += stride) digit_hist[i] = 0;
+  const uint32_t nl = n_lookback * (uint32_t)passes;
+  for (uint32_t i = tid; i < nl; i += stride) lookback[i] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// bbox: exact FP32 min / max per frame (order-preserving integer atomics);
+// flags non-finite coordinates.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kFrontThreads) k_bbox(const float *__restrict__ xyz,
+                                                        FrameInfo *frames, const Tile *__restrict__ tiles,
+                                                        Counters *ctr) {
+  const Tile t = tiles[blockIdx.x];
+  uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, mx[3] = {0u, 0u, 0u};
+  bool bad = false;
+  for (uint32_t i = t.begin + threadIdx.x; i < t.end; i += kFrontThreads) {
+    for (int a = 0; a < 3; ++a) {
+      float v = xyz[3ull * i + a];
+      bad |= !isfinite(v);
+      uint32_t o = f2ord(v);
+      mn[a] = min(mn[a], o);
+      mx[a] = max(mx[a], o);
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    for (int off = 16; off; off >>= 1) {
+      mn[a] = min(mn[a], __shfl_xor_sync(0xFFFFFFFFu, mn[a], off));
+      mx[a] = max(mx[a], __shfl_xor_sync(0xFFFFFFFFu, mx[a], off));
+    }
+  }
+  bad = __any_sync(0xFFFFFFFFu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    FrameInfo &f = frames[t.frame];
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(&f.lo_ord[a], mn[a]);
+      atomicMax(&f.hi_ord[a], mx[a]);
+    }
+    if (bad) atomicOr(&ctr->status, kStNonFinite);
+  }
+}
+
+// Root cube of a frame from its reduced extents (reading: anchored at the FP32
+// minimum, side = largest FP32 extent, 1 if the frame is a single location).
+__device__ __forceinline__ void root_cube(const FrameInfo &f, float lo[3], float &side, float &s) {
+  side = 0.0f;
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = ord2f(f.lo_ord[a]);
+    float e = __fsub_rn(ord2f(f.hi_ord[a]), lo[a]);
+    side = (e > side) ? e : side;
+  }
+  if (side == 0.0f) side = 1.0f;
+  s = __fdiv_rn(2097152.0f, side);
+}
+
+// ---------------------------------------------------------------------------
+// keys: 63-bit Morton key per point, value = global point index; the first
+// tile of each frame publishes the frame's root cube for later kernels.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kFrontThreads) k_keys(const float *__restrict__ xyz, FrameInfo *frames,
+                                                        const Tile *__restrict__ tiles,
+                                                        unsigned long long *__restrict__ keys,
+                                                        uint32_t *__restrict__ vals, uint64_t *dbg_key,
+                                                        const Counters *ctr) {
+  if (ctr->status & kStFatal) return;
+  const Tile t = tiles[blockIdx.x];
+  float lo[3], side, s;
+  root_cube(frames[t.frame], lo, side, s);
+  if (blockIdx.x == t.first_tile && threadIdx.x == 0) {
+    FrameInfo &f = frames[t.frame];
+    f.lo[0] = lo[0];
+    f.lo[1] = lo[1];
+    f.lo[2] = lo[2];
+    f.side = side;
+    f.s = s;
+    f.delta = __fmul_rn(side, kInvTwo21);
+  }
+  for (uint32_t i = t.begin + threadIdx.x; i < t.end; i += kFrontThreads) {
+    uint32_t q0 = quantise(xyz[3ull * i + 0], lo[0], s);
+    uint32_t q1 = quantise(xyz[3ull * i + 1], lo[1], s);
+    uint32_t q2 = quantise(xyz[3ull * i + 2], lo[2], s);
+    unsigned long long k = morton3(q0, q1, q2);
+    keys[i] = k;
+    vals[i] = i;
+    if (dbg_key) dbg_key[i] = k;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// upfront digit histograms of every pass, per frame
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kFrontThreads) k_digit_hist(const unsigned long long *__restrict__ keys,
+                                                              const Tile *__restrict__ tiles,
+                                                              uint32_t *__restrict__ hist, int lowbit,
+                                                              int passes, const Counters *ctr) {
+  __shared__ uint32_t sh[kMaxPasses][256];
+  if (ctr->status & kStFatal) return;
+  for (int i = threadIdx.x; i < kMaxPasses * 256; i += kFrontThreads) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  const Tile t = tiles[blockIdx.x];
+  for (uint32_t i = t.begin + threadIdx.x; i < t.end; i += kFrontThreads) {
+    unsigned long long k = keys[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k >> (lowbit + 8 * p)) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  uint32_t *h = hist + (size_t)t.frame * kMaxPasses * 256;
+  for (int i = threadIdx.x; i < passes * 256; i += kFrontThreads) {
+    uint32_t v = (&sh[0][0])[i];
+    if (v) atomicAdd(&h[i], v);
+  }
+}
+
+// exclusive scan of each (frame, pass) digit histogram -> absolute output bases
+__global__ void __launch_bounds__(256) k_digit_scan(const uint32_t *__restrict__ hist,
+                                                    uint32_t *__restrict__ base,
+                                                    const FrameInfo *__restrict__ frames, int passes,
+                                                    const Counters *ctr) {
+  __shared__ uint32_t warp_tot[8];
+  if (ctr->status & kStFatal) return;
+  const uint32_t f = blockIdx.x / passes, p = blockIdx.x % passes;
+  const size_t off = ((size_t)f * kMaxPasses + p) * 256;
+  const uint32_t d = threadIdx.x, lane = d & 31, w = d >> 5;
+  uint32_t v = hist[off + d], x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  uint32_t wp = 0;
+  for (uint32_t i = 0; i < w; ++i) wp += warp_tot[i];
+  base[off + d] = frames[f].begin + wp + x - v;
+}
+
+// ---------------------------------------------------------------------------
+// one radix pass (stable, segmented by frame, decoupled look-back)
+// ---------------------------------------------------------------------------
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kValMask = (1u << 30) - 1u;
+
+template <bool kLast>
+__global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
+    const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
+    unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout, float4 *__restrict__ pout,
+    const float *__restrict__ xyz, const Tile *__restrict__ tiles, const FrameInfo *__restrict__ frames,
+    const uint32_t *__restrict__ digit_base, uint32_t *__restrict__ lookback, uint32_t *tile_counter,
+    int shift, Counters *ctr) {
+  constexpr int W = kFrontThreads / 32;
+  __shared__ uint32_t s_wcnt[W][256];
+  __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_fail;
+  if (ctr->status & kStFatal) return;
+  for (int i = threadIdx.x; i < W * 256; i += kFrontThreads) (&s_wcnt[0][0])[i] = 0;
+  if (threadIdx.x == 0) {
+    s_tile = atomicAdd(tile_counter, 1u);  // dynamic tile order: forward progress of look-back
+    s_fail = 0;
+  }
+  __syncthreads();
+  const uint32_t ti = s_tile;
+  const Tile t = tiles[ti];
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t wbase = t.begin + w * 32 * kFrontItems;
+
+  unsigned long long key[kFrontItems];
+  uint32_t val[kFrontItems], dig[kFrontItems], rank[kFrontItems];
+#pragma unroll
+  for (int i = 0; i < kFrontItems; ++i) {
+    uint32_t idx = wbase + i * 32 + lane;
+    bool ok = idx < t.end;
+    key[i] = ok ? kin[idx] : ~0ull;
+    val[i] = ok ? vin[idx] : 0u;
+    dig[i] = ok ? (uint32_t)((key[i] >> shift) & 0xFFu) : 256u;
+  }
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < kFrontItems; ++i) {
+    const uint32_t d = dig[i];
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    uint32_t old = 0;
+    if (d < 256u) old = s_wcnt[w][d];
+    __syncwarp();
+    rank[i] = old + __popc(peers & lt);
+    if (d < 256u && (peers & lt) == 0) s_wcnt[w][d] = old + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: exclusive prefix over warps, tile total, then look-back
+  {
+    const uint32_t d = threadIdx.x;
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < W; ++ww) {
+      uint32_t c = s_wcnt[ww][d];
+      s_wcnt[ww][d] = run;
+      run += c;
+    }
+    uint32_t *lb = lookback + (size_t)ti * 256;
+    uint32_t excl = 0;
+    if (ti == t.first_tile) {
+      atomicExch(&lb[d], kFlagInc | run);
+    } else {
+      atomicExch(&lb[d], kFlagAgg | run);
+      for (int32_t tp = (int32_t)ti - 1; tp >= (int32_t)t.first_tile; --tp) {
+        const uint32_t *q = lookback + (size_t)tp * 256 + d;
+        uint32_t wv = 0;
+        uint32_t it = 0;
+        for (; it < kSpinLimit; ++it) {
+          wv = ld_volatile(q);
+          if (wv & (kFlagAgg | kFlagInc)) break;
+          if (it > 32) __nanosleep(64);
+        }
+        if (it == kSpinLimit) {
+          atomicOr(&ctr->status, kStTimeout);
+          s_fail = 1;
+          break;
+        }
+        excl += wv & kValMask;
+        if (wv & kFlagInc) break;
+      }
+      atomicExch(&lb[d], kFlagInc | (excl + run));
+    }
+    s_base[d] = digit_base[(size_t)t.frame * kMaxPasses * 256 + d] + excl;
+  }
+  __syncthreads();
+  if (s_fail) return;
+  const uint32_t fend = frames[t.frame].end, fbeg = frames[t.frame].begin;
+#pragma unroll
+  for (int i = 0; i < kFrontItems; ++i) {
+    const uint32_t d = dig[i];
+    if (d >= 256u) continue;
+    const uint32_t pos = s_base[d] + s_wcnt[w][d] + rank[i];
+    if (pos < fbeg || pos >= fend) {
+      atomicOr(&ctr->status, kStInternal);
+      continue;
+    }
+    kout[pos] = key[i];
+    if (kLast) {
+      const uint32_t v = val[i];
+      if (v >= fend) {  // values are point indices of this batch; never read out of bounds
+        atomicOr(&ctr->status, kStInternal);
+        continue;
+      }
+      pout[pos] = make_float4(xyz[3ull * v], xyz[3ull * v + 1], xyz[3ull * v + 2], __uint_as_float(v));
+    } else {
+      vout[pos] = val[i];
+    }
+  }
+}
+
+// Without a sort (max_depth 0: one leaf per frame) the points are packed as is.
+__global__ void k_pack(const float *__restrict__ xyz, const Tile *__restrict__ tiles,
+                       float4 *__restrict__ pout, const Counters *ctr) {
+  if (ctr->status & kStFatal) return;
+  const Tile t = tiles[blockIdx.x];
+  for (uint32_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x)
+    pout[i] = make_float4(xyz[3ull * i], xyz[3ull * i + 1], xyz[3ull * i + 2], __uint_as_float(i));
+}
+
+// ---------------------------------------------------------------------------
+// leaf finder
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long prefix_of(unsigned long long k, int level) {
+  return level == 0 ? 0ull : (k >> (63 - 3 * level));
+}
+
+// first index in [lo, hi) whose level-L prefix is >= pre (keys sorted)
+__device__ __forceinline__ uint32_t lower_pre(const unsigned long long *keys, uint32_t lo, uint32_t hi,
+                                              unsigned long long pre, int level) {
+  while (lo < hi) {
+    uint32_t mid = lo + ((hi - lo) >> 1);
+    if (prefix_of(keys[mid], level) < pre) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+// first index in [lo, hi) whose level-L prefix is > pre
+__device__ __forceinline__ uint32_t upper_pre(const unsigned long long *keys, uint32_t lo, uint32_t hi,
+                                              unsigned long long pre, int level) {
+  while (lo < hi) {
+    uint32_t mid = lo + ((hi - lo) >> 1);
+    if (prefix_of(keys[mid], level) <= pre) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// A sorted position i starts a leaf iff it starts its frame, or every octree
+// node shared with position i-1 holds more than leaf_capacity points (so the
+// leaf of i is a proper descendant of the deepest shared node, and begins at i).
+__global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long long *__restrict__ keys,
+                                                          const Tile *__restrict__ tiles,
+                                                          const FrameInfo *__restrict__ frames,
+                                                          Leaf *__restrict__ leaves, Counters *ctr,
+                                                          uint32_t cap, int D) {
+  if (ctr->status & kStFatal) return;
+  const Tile t = tiles[blockIdx.x];
+  const uint32_t fb = frames[t.frame].begin, fe = frames[t.frame].end;
+  for (uint32_t i = t.begin + threadIdx.x; i < t.end; i += kFrontThreads) {
+    const unsigned long long ki = keys[i];
+    int L;  // level of the first node that starts at i
+    if (i == fb) {
+      L = 0;
+    } else {
+      const unsigned long long x = keys[i - 1] ^ ki;
+      int l = (x == 0) ? 21 : (__clzll((long long)x) - 1) / 3;  // shared levels below the root
+      if (l >= D) continue;                                      // same max-depth node
+      // count of the level-l node containing i-1 and i, decided within a window
+      bool big;
+      if (l == 0) {
+        big = (fe - fb) > cap;
+      } else {
+        const unsigned long long pre = prefix_of(ki, l);
+        const uint32_t wlo = (i - fb > cap + 1) ? i - cap - 1 : fb;
+        const uint32_t whi = (fe - i > cap + 1) ? i + cap + 1 : fe;
+        const uint32_t a = lower_pre(keys, wlo, i, pre, l);
+        const uint32_t b = upper_pre(keys, i, whi, pre, l);
+        big = (b - a) > cap;
+      }
+      if (!big) continue;
+      L = l + 1;
+    }
+    // descend from the level-L node starting at i to the leaf containing i
+    for (;; ++L) {
+      const unsigned long long pre = prefix_of(ki, L);
+      uint32_t e;
+      if (L < D) {
+        const uint32_t whi = (fe - i > cap + 1) ? i + cap + 1 : fe;
+        e = upper_pre(keys, i, whi, pre, L);
+        if (e - i > cap) continue;
+      } else {
+        e = upper_pre(keys, i, fe, pre, L);
+      }
+      const uint32_t slot = atomicAdd(&ctr->n_leaves, 1u);
+      leaves[slot] = Leaf{i, e - i, t.frame, (uint32_t)L};
+      break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launcher
+// ---------------------------------------------------------------------------
+int front_passes(int max_depth) { return (3 * max_depth + 7) / 8; }
+
+int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t *ev_after_keys,
+                 cudaEvent_t *ev_after_sort) {
+  const int passes = front_passes(a.max_depth);
+  const int lowbit = 63 - 3 * a.max_depth;
+  const uint32_t nlb = a.ntiles * 256u;
+  int nl = 0;
+  {
+    uint32_t work = a.nframes * kMaxPasses * 256u;
+    if (nlb * (uint32_t)passes > work) work = nlb * (uint32_t)passes;
+    uint32_t blocks = (work + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 4096) blocks = 4096;
+    k_init<<<blocks, 256, 0, st>>>(a.frames, a.nframes, a.ctr, a.digit_hist, a.lookback, nlb, passes);
+    ++nl;
+  }
+  k_bbox<<<a.ntiles, kFrontThreads, 0, st>>>(a.xyz, a.frames, a.tiles, a.ctr);
+  k_keys<<<a.ntiles, kFrontThreads, 0, st>>>(a.xyz, a.frames, a.tiles, a.keys[0], a.vals[0], a.dbg_key, a.ctr);
+  nl += 2;
+  if (ev_after_keys) cudaEventRecord(*ev_after_keys, st);
+  int cur = 0;
+  if (passes > 0) {
+    k_digit_hist<<<a.ntiles, kFrontThreads, 0, st>>>(a.keys[0], a.tiles, a.digit_hist, lowbit, passes, a.ctr);
+    k_digit_scan<<<a.nframes * passes, 256, 0, st>>>(a.digit_hist, a.digit_base, a.frames, passes, a.ctr);
+    nl += 2;
+    for (int p = 0; p < passes; ++p) {
+      const int shift = lowbit + 8 * p;
+      const uint32_t *base = a.digit_base + p * 256;
+      uint32_t *lb = a.lookback + (size_t)p * nlb;
+      if (p == passes - 1) {
+        k_radix_pass<true><<<a.ntiles, kFrontThreads, 0, st>>>(
+            a.keys[cur], a.vals[cur], a.keys[cur ^ 1], a.vals[cur ^ 1], a.spts, a.xyz, a.tiles, a.frames,
+            base, lb, &a.ctr->tile_work[p], shift, a.ctr);
+      } else {
+        k_radix_pass<false><<<a.ntiles, kFrontThreads, 0, st>>>(
+            a.keys[cur], a.vals[cur], a.keys[cur ^ 1], a.vals[cur ^ 1], a.spts, a.xyz, a.tiles, a.frames,
+            base, lb, &a.ctr->tile_work[p], shift, a.ctr);
+      }
+      cur ^= 1;
+      ++nl;
+    }
+  } else {
+    k_pack<<<a.ntiles, kFrontThreads, 0, st>>>(a.xyz, a.tiles, a.spts, a.ctr);
+    ++nl;
+  }
+  if (ev_after_sort) cudaEventRecord(*ev_after_sort, st);
+  k_leaves<<<a.ntiles, kFrontThreads, 0, st>>>(a.keys[cur], a.tiles, a.frames, a.leaves, a.ctr,
+                                               a.leaf_capacity, a.max_depth);
+  ++nl;
+  if (launches) *launches += nl;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace gd

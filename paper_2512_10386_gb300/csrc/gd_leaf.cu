@@ -1,0 +1,674 @@
+// gd_leaf.cu -- the per-leaf part of the method, fused into one persistent kernel.
+//
+// Each CTA pulls octree leaves from a device work counter and runs, for one
+// leaf at a time, every per-leaf step of Sec. 3 in shared memory:
+//   extents and adaptive voxel size h (Eq. 10-11) -> voxel occupancy counts in a
+//   shared hash table with warp-aggregated atomics, voxel gate (Eq. 12) and
+//   compaction of P_1 -> tie ranks (input-index order) by bitonic sort -> kNN of
+//   every P_1 point against the leaf's P_1 (register top-K, candidates
+//   broadcast from shared memory), r_K (Eq. 13) -> exact percentile gate
+//   (Eq. 14) as a rank cut on r_K^2 -> median density (Eq. 16) -> dual-weight
+//   gravitational score (Eq. 15-21) -> Top-lambda or log-threshold selection,
+//   scattered to input order (Eq. 22).
+// The leaf's points arrive in shared memory by one TMA bulk copy
+// (cp.async.bulk + mbarrier).  Leaves larger than the shared-memory capacity
+// (only possible at max depth, i.e. with massive duplicates) run the same code
+// on a per-point spill area in global memory.
+//
+// FP32 steps that decide integers (voxel indices, neighbour order, the density
+// rank cut) use explicitly rounded intrinsics so no FMA contraction can change
+// them; FP64 per-leaf scalars (V_t, h, rho_med) use explicitly rounded FP64.
+#include "gd_common.cuh"
+
+namespace gd {
+
+constexpr int kLeafThreads = 128;
+constexpr int kLeafWarps = kLeafThreads / 32;
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr unsigned long long kInvalid = ~0ull - 1ull;
+
+__host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ __forceinline__ uint32_t pow2ceil(uint32_t x) {
+  uint32_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Per-leaf working arrays: shared memory (small leaves) or global spill (large).
+struct LeafMem {
+  float4 *p1;                // [cap] P_1 points; w = input index, then tie rank
+  unsigned long long *hkey;  // [hcap] voxel hash keys
+  uint32_t *hcnt;            // [hcap] voxel occupancy
+  unsigned long long *sbuf;  // [scap] sort buffer
+  float *r2, *wa, *wc, *F;   // [cap] per P_1 position
+  uint32_t *gidx;            // [cap] global input index per P_1 position
+  uint32_t *por;             // [cap] P_1 position of each tie rank
+  uint8_t *flag;             // [cap] 0 removed by density gate, 1 scored, 2 kept
+  void *nbr;                 // [cap][KMAX] neighbour positions
+  uint32_t hcap, scap;
+};
+
+// Layout of the per-leaf arrays.  `alias_head` bytes at the start (the TMA
+// landing zone of the leaf's raw points) are shared with the hash table and
+// the neighbour table, whose lifetimes do not overlap with it.
+template <typename IdxT>
+__host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t cap, int kmax, LeafMem *m,
+                                                 size_t head_bytes) {
+  const uint32_t hcap = pow2ceil(2 * cap), scap = pow2ceil(cap);
+  // region A: max(raw points + hash table, neighbour table)
+  const size_t hash_off = al16(head_bytes);
+  const size_t hash_end = hash_off + al16((size_t)hcap * 8) + al16((size_t)hcap * 4);
+  const size_t nbr_bytes = al16((size_t)cap * kmax * sizeof(IdxT));
+  size_t off = hash_end > nbr_bytes ? hash_end : nbr_bytes;
+  off = al16(off);
+  if (m) {
+    m->hkey = (unsigned long long *)(base + hash_off);
+    m->hcnt = (uint32_t *)(base + hash_off + al16((size_t)hcap * 8));
+    m->nbr = (void *)base;
+    m->hcap = hcap;
+    m->scap = scap;
+  }
+  size_t o = off;
+  auto take = [&](size_t bytes) { size_t r = o; o = al16(o + bytes); return r; };
+  const size_t p1 = take((size_t)cap * 16), sb = take((size_t)scap * 8);
+  const size_t r2 = take((size_t)cap * 4), wa = take((size_t)cap * 4), wc = take((size_t)cap * 4);
+  const size_t F = take((size_t)cap * 4), gi = take((size_t)cap * 4), po = take((size_t)cap * 4);
+  const size_t fl = take((size_t)cap);
+  if (m) {
+    m->p1 = (float4 *)(base + p1);
+    m->sbuf = (unsigned long long *)(base + sb);
+    m->r2 = (float *)(base + r2);
+    m->wa = (float *)(base + wa);
+    m->wc = (float *)(base + wc);
+    m->F = (float *)(base + F);
+    m->gidx = (uint32_t *)(base + gi);
+    m->por = (uint32_t *)(base + po);
+    m->flag = (uint8_t *)(base + fl);
+  }
+  return o;
+}
+
+struct LeafShared {
+  uint32_t leaf;
+  uint32_t n1, keff, m, keep_n, run;
+  uint32_t Rbits;
+  float lo[3], h, delta, r2ref, Lref;
+  double rho_med;
+  uint32_t wsum[kLeafWarps];
+  uint32_t red[kLeafWarps][6];
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+// Eq. 11 cube root: u = m 2^e (frexp), y0 = 2^floor(e/3), ten Newton steps
+// y <- y - (y*y*y - u) / (3*(y*y)), every operation rounded in FP64.
+__device__ __forceinline__ double cbrt_spec(double u) {
+  int e = 0;
+  (void)frexp(u, &e);
+  const int k = (e >= 0) ? e / 3 : -((-e + 2) / 3);
+  double y = ldexp(1.0, k);
+#pragma unroll 1
+  for (int it = 0; it < 10; ++it) {
+    const double y2 = __dmul_rn(y, y);
+    const double y3 = __dmul_rn(y2, y);
+    y = __dsub_rn(y, __ddiv_rn(__dsub_rn(y3, u), __dmul_rn(3.0, y2)));
+  }
+  return y;
+}
+
+__device__ __forceinline__ uint32_t vox_index(float x, float lo, float h) {
+  const float f = floorf(__fdiv_rn(__fsub_rn(x, lo), h));
+  return (f < 2097151.0f) ? (uint32_t)f : kQMax;
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t hash_insert(unsigned long long *hk, uint32_t hcap, unsigned long long key,
+                                                Counters *ctr) {
+  const uint32_t mask = hcap - 1;
+  uint32_t s = (uint32_t)mix64(key) & mask;
+  for (uint32_t probe = 0; probe < hcap; ++probe) {
+    const unsigned long long prev = atomicCAS(hk + s, kEmpty, key);
+    if (prev == kEmpty || prev == key) return s;
+    s = (s + 1) & mask;
+  }
+  atomicOr(&ctr->status, kStInternal);
+  return s;
+}
+
+__device__ __forceinline__ uint32_t hash_find(const unsigned long long *hk, uint32_t hcap,
+                                              unsigned long long key) {
+  const uint32_t mask = hcap - 1;
+  uint32_t s = (uint32_t)mix64(key) & mask;
+  for (uint32_t probe = 0; probe < hcap; ++probe) {
+    if (hk[s] == key) return s;
+    s = (s + 1) & mask;
+  }
+  return 0xFFFFFFFFu;
+}
+
+// ascending bitonic sort of n (power of two) keys by the whole block
+__device__ void bitonic_sort(unsigned long long *a, uint32_t n) {
+  for (uint32_t k = 2; k <= n; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < n; i += kLeafThreads) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const unsigned long long x = a[i], y = a[l];
+          const bool asc = (i & k) == 0;
+          if ((x > y) == asc) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// squared distance with the fixed FP32 operation order of the method's reading:
+// dx = x_j - x_i;  d^2 = fma(dz, dz, fma(dy, dy, dx*dx))
+__device__ __forceinline__ float sqdist(const float4 &a, const float4 &b) {
+  const float dx = __fsub_rn(b.x, a.x), dy = __fsub_rn(b.y, a.y), dz = __fsub_rn(b.z, a.z);
+  return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// Sorted register lists (ascending); insert c and drop the largest:
+// L'[s] = min(L[s], max(L[s-1], c)), L'[0] = min(L[0], c).  Every slot uses the
+// old neighbour value, so the KMAX updates are independent (no serial chain).
+template <int KMAX>
+__device__ __forceinline__ void topk_insert_f(float (&L)[KMAX], float c) {
+#pragma unroll
+  for (int s = KMAX - 1; s > 0; --s) L[s] = fminf(L[s], fmaxf(L[s - 1], c));
+  L[0] = fminf(L[0], c);
+}
+template <int KMAX>
+__device__ __forceinline__ void topk_insert_u(uint32_t (&L)[KMAX], uint32_t c) {
+#pragma unroll
+  for (int s = KMAX - 1; s > 0; --s) L[s] = min(L[s], max(L[s - 1], c));
+  L[0] = min(L[0], c);
+}
+
+__device__ __forceinline__ void write_point(const LeafArgs &A, uint32_t g, uint8_t mk, float sc, uint8_t st) {
+  if (g >= A.n) {  // cannot happen with a consistent sort; never write out of bounds
+    atomicOr(&A.ctr->status, kStInternal);
+    return;
+  }
+  if (A.mask) A.mask[g] = mk;
+  if (A.score) A.score[g] = sc;
+  if (A.stage) A.stage[g] = st;
+  if (A.use_train) {
+    A.train.stage[g] = st;
+    A.train.F[g] = sc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one leaf
+// ---------------------------------------------------------------------------
+template <int KMAX, typename IdxT>
+__device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__restrict__ pts, const LeafMem &M,
+                             LeafShared &S) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t nt = lf.count;
+  const denoise_params &P = A.p;
+  const uint32_t lt = lanemask_lt();
+  IdxT *nbr = (IdxT *)M.nbr;
+
+  // ---- Eq. 10-11: leaf bounding box, floored extents, adaptive voxel size
+  {
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (uint32_t i = tid; i < nt; i += kLeafThreads) {
+      const float4 p = pts[i];
+      mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
+      mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      for (int o = 16; o; o >>= 1) {
+        mn[a] = fminf(mn[a], __shfl_xor_sync(0xFFFFFFFFu, mn[a], o));
+        mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xFFFFFFFFu, mx[a], o));
+      }
+    }
+    if (lane == 0) {
+      for (int a = 0; a < 3; ++a) {
+        S.red[w][a] = __float_as_uint(mn[a]);
+        S.red[w][3 + a] = __float_as_uint(mx[a]);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float lo[3], hi[3];
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = __uint_as_float(S.red[0][a]);
+        hi[a] = __uint_as_float(S.red[0][3 + a]);
+        for (int ww = 1; ww < kLeafWarps; ++ww) {
+          lo[a] = fminf(lo[a], __uint_as_float(S.red[ww][a]));
+          hi[a] = fmaxf(hi[a], __uint_as_float(S.red[ww][3 + a]));
+        }
+      }
+      const float delta = A.frames[lf.frame].delta;
+      double H[3];
+      for (int a = 0; a < 3; ++a) {
+        float e = __fsub_rn(hi[a], lo[a]);
+        if (e < delta) e = delta;
+        H[a] = (double)e;
+        S.lo[a] = lo[a];
+      }
+      const double V = __dmul_rn(__dmul_rn(H[0], H[1]), H[2]);
+      const double u = __ddiv_rn(V, (double)nt);
+      S.h = __double2float_rn(__dmul_rn((double)P.beta, cbrt_spec(u)));
+      S.delta = delta;
+      S.run = 0;
+    }
+  }
+  // ---- Eq. 12: voxel occupancy (hash with warp-aggregated atomics)
+  const uint32_t hcap = pow2ceil(2 * nt);  // <= the carved capacity
+  for (uint32_t i = tid; i < hcap; i += kLeafThreads) {
+    M.hkey[i] = kEmpty;
+    M.hcnt[i] = 0;
+  }
+  __syncthreads();
+  const float lo0 = S.lo[0], lo1 = S.lo[1], lo2 = S.lo[2], h = S.h;
+  for (uint32_t base = 0; base < nt; base += kLeafThreads) {
+    const uint32_t i = base + tid;
+    unsigned long long key = kInvalid;
+    if (i < nt) {
+      const float4 p = pts[i];
+      key = ((unsigned long long)vox_index(p.x, lo0, h) << 42) |
+            ((unsigned long long)vox_index(p.y, lo1, h) << 21) | (unsigned long long)vox_index(p.z, lo2, h);
+    }
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
+    if (i < nt && (peers & lt) == 0) {
+      const uint32_t s = hash_insert(M.hkey, hcap, key, A.ctr);
+      atomicAdd(M.hcnt + s, (uint32_t)__popc(peers));
+    }
+  }
+  __syncthreads();
+  // lookup, gate, compaction of P_1 (order preserved)
+  const uint32_t fbeg = A.frames[lf.frame].begin;
+  for (uint32_t base = 0; base < nt; base += kLeafThreads) {
+    const uint32_t i = base + tid;
+    bool in1 = false;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t g = 0;
+    if (i < nt) {
+      p = pts[i];
+      g = __float_as_uint(p.w);
+      if (g >= A.n) {
+        atomicOr(&A.ctr->status, kStInternal);
+        g = 0;
+      }
+      const unsigned long long key = ((unsigned long long)vox_index(p.x, lo0, h) << 42) |
+                                     ((unsigned long long)vox_index(p.y, lo1, h) << 21) |
+                                     (unsigned long long)vox_index(p.z, lo2, h);
+      const uint32_t s = hash_find(M.hkey, hcap, key);
+      const uint32_t c = (s == 0xFFFFFFFFu) ? 0u : M.hcnt[s];
+      in1 = c >= P.min_vox_count;
+      if (A.use_dbg) {
+        if (A.dbg.vox_count) A.dbg.vox_count[g] = c;
+        if (A.dbg.leaf_start) A.dbg.leaf_start[g] = lf.start - fbeg;
+        if (A.dbg.leaf_count) A.dbg.leaf_count[g] = nt;
+        if (A.dbg.leaf_h) A.dbg.leaf_h[g] = h;
+        if (A.dbg.leaf_rho_med) A.dbg.leaf_rho_med[g] = 0.0;
+        if (A.dbg.r2) A.dbg.r2[g] = 0.0f;
+      }
+      if (!in1) write_point(A, g, 0, 0.0f, 1);
+    }
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, in1);
+    if (lane == 0) S.wsum[w] = __popc(bal);
+    __syncthreads();
+    uint32_t off = S.run;
+    for (uint32_t ww = 0; ww < w; ++ww) off += S.wsum[ww];
+    if (in1) {
+      const uint32_t pos = off + __popc(bal & lt);
+      M.p1[pos] = p;
+      M.gidx[pos] = g;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t t = 0;
+      for (int ww = 0; ww < kLeafWarps; ++ww) t += S.wsum[ww];
+      S.run += t;
+    }
+    __syncthreads();
+  }
+  const uint32_t n1 = S.run;
+  if (n1 <= 1) {  // no neighbour exists: the density gate cannot keep it
+    for (uint32_t i = tid; i < n1; i += kLeafThreads) write_point(A, M.gidx[i], 0, 0.0f, 2);
+    return;
+  }
+  const uint32_t keff = (P.k < n1 - 1) ? P.k : n1 - 1;
+  if (tid == 0) {
+    atomicAdd(&A.ctr->knn_pairs, (unsigned long long)n1 * (unsigned long long)(n1 - 1));
+    atomicAdd(&A.ctr->n_p1, (unsigned long long)n1);
+  }
+  // ---- tie ranks: order of input index among P_1
+  const uint32_t sn = pow2ceil(n1);
+  for (uint32_t i = tid; i < sn; i += kLeafThreads)
+    M.sbuf[i] = (i < n1) ? (((unsigned long long)M.gidx[i] << 32) | i) : kEmpty;
+  __syncthreads();
+  bitonic_sort(M.sbuf, sn);
+  for (uint32_t r = tid; r < n1; r += kLeafThreads) {
+    const uint32_t pos = (uint32_t)(M.sbuf[r] & 0xFFFFFFFFu);
+    M.por[r] = pos;
+    M.p1[pos].w = __uint_as_float(r);
+  }
+  __syncthreads();
+
+  // ---- kNN on P_1 (excluding self), order by (d^2, input index).
+  // Phase A: the k_eff-th smallest d^2, theta, with a register min/max network on
+  // FP32 values only (placeholders -1 fill the unused KMAX - k_eff slots).
+  // Phase B: a second scan keeps every candidate with d^2 < theta and, among the
+  // candidates at exactly theta, the ones with the smallest input-index ranks.
+  // The set is the k_eff smallest by (d^2, input index), as with a full sort.
+  const float delta2 = __fmul_rn(S.delta, S.delta);
+  for (uint32_t qb = 0; qb < n1; qb += kLeafThreads) {
+    const uint32_t q = qb + tid;
+    if (q < n1) {
+      const float4 me = M.p1[q];
+      const uint32_t j0 = qb + w * 32;  // start near the warp's own queries (spatially local)
+      float L[KMAX];
+#pragma unroll
+      for (int s = 0; s < KMAX; ++s) L[s] = (s < KMAX - (int)keff) ? -1.0f : INFINITY;
+      for (uint32_t j = j0, c = 0; c < n1; ++c, j = (j + 1 == n1) ? 0 : j + 1) {
+        if (j == q) continue;
+        const float d2 = sqdist(me, M.p1[j]);
+        if (d2 < L[KMAX - 1]) topk_insert_f<KMAX>(L, d2);
+      }
+      const float theta = L[KMAX - 1];
+      uint32_t below = 0;
+#pragma unroll
+      for (int s = 0; s < KMAX; ++s) below += (L[s] >= 0.0f && L[s] < theta) ? 1u : 0u;
+      const uint32_t ties_needed = keff - below;
+      uint32_t T[KMAX];
+#pragma unroll
+      for (int s = 0; s < KMAX; ++s) T[s] = 0xFFFFFFFFu;
+      const uint32_t gq = M.gidx[q];
+      const bool dbg_n = A.use_dbg && A.dbg.nbr, dbg_d = A.use_dbg && A.dbg.nbr_d2;
+      uint32_t a = 0;
+      for (uint32_t j = j0, c = 0; c < n1; ++c, j = (j + 1 == n1) ? 0 : j + 1) {
+        if (j == q) continue;
+        const float4 cj = M.p1[j];
+        const float d2 = sqdist(me, cj);
+        if (d2 < theta) {
+          if (a < keff) {
+            nbr[(size_t)q * KMAX + a] = (IdxT)j;
+            if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + a] = M.gidx[j];
+            if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + a] = d2;
+            if (A.use_train) {
+              A.train.nbr[(size_t)gq * P.k + a] = M.gidx[j];
+              A.train.nd2[(size_t)gq * P.k + a] = d2;
+            }
+          }
+          ++a;
+        } else if (d2 == theta) {
+          const uint32_t rk = __float_as_uint(cj.w);
+          if (rk < T[KMAX - 1]) topk_insert_u<KMAX>(T, rk);
+        }
+      }
+      if (a != below) atomicOr(&A.ctr->status, kStInternal);  // the two scans must agree
+#pragma unroll
+      for (int s = 0; s < KMAX; ++s) {
+        if ((uint32_t)s < ties_needed && below + s < keff) {
+          const uint32_t t = below + s;
+          const uint32_t npos = (T[s] < n1) ? M.por[T[s]] : 0u;
+          nbr[(size_t)q * KMAX + t] = (IdxT)npos;
+          if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = M.gidx[npos];
+          if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = theta;
+          if (A.use_train) {
+            A.train.nbr[(size_t)gq * P.k + t] = M.gidx[npos];
+            A.train.nd2[(size_t)gq * P.k + t] = theta;
+          }
+        }
+      }
+      for (uint32_t t = keff; t < P.k; ++t) {
+        if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
+        if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = 0.0f;
+        if (A.use_train) {
+          A.train.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
+          A.train.nd2[(size_t)gq * P.k + t] = 0.0f;
+        }
+      }
+      const float rt = (theta < delta2) ? delta2 : theta;
+      M.r2[q] = rt;
+      if (A.use_dbg && A.dbg.r2) A.dbg.r2[gq] = rt;
+      if (A.use_train) A.train.r2[gq] = rt;
+    }
+  }
+  __syncthreads();
+
+  // ---- Eq. 14: exact percentile cut, as a rank cut on r_K^2 (rho decreasing in r_K)
+  for (uint32_t i = tid; i < sn; i += kLeafThreads)
+    M.sbuf[i] = (i < n1) ? (((unsigned long long)__float_as_uint(M.r2[i]) << 32) | i) : kEmpty;
+  __syncthreads();
+  bitonic_sort(M.sbuf, sn);
+  if (tid == 0) {
+    const double pos = __dadd_rn(__ddiv_rn(__dmul_rn((double)n1, (double)P.rho_percentile), 100.0), 0.5);
+    const double cc = ceil(pos);
+    const uint32_t c = (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;
+    S.Rbits = (uint32_t)(M.sbuf[n1 - c] >> 32);
+  }
+  __syncthreads();
+  const uint32_t Rb = S.Rbits;
+  for (uint32_t i = tid; i < n1; i += kLeafThreads) {
+    const uint32_t v = (uint32_t)(M.sbuf[i] >> 32);
+    if (v <= Rb && (i + 1 == n1 || (uint32_t)(M.sbuf[i + 1] >> 32) > Rb)) S.m = i + 1;
+    M.flag[i] = (__float_as_uint(M.r2[i]) <= Rb) ? 1 : 0;
+  }
+  __syncthreads();
+  const uint32_t m = S.m;
+  // ---- Eq. 16: median density over P_2; per-leaf constants in FP64
+  if (tid == 0) {
+    const double k43pi = (4.0 / 3.0) * 3.14159265358979323846;
+    auto rho_of = [&](uint32_t bits) {
+      const double rr = (double)__uint_as_float(bits);
+      return (double)keff / __dmul_rn(k43pi, __dmul_rn(rr, sqrt(rr)));
+    };
+    const uint32_t mid = (m - 1) / 2;
+    double rho_med;
+    if (m & 1u) rho_med = rho_of((uint32_t)(M.sbuf[mid] >> 32));
+    else rho_med = 0.5 * (rho_of((uint32_t)(M.sbuf[m / 2 - 1] >> 32)) + rho_of((uint32_t)(M.sbuf[m / 2] >> 32)));
+    const double D2 = __dadd_rn(__dmul_rn(rho_med, rho_med), (double)P.eps_rho);
+    const uint32_t refb = (uint32_t)(M.sbuf[mid] >> 32);
+    S.r2ref = __uint_as_float(refb);
+    S.Lref = (float)(log2(rho_of(refb)) - 0.5 * log2(D2));
+    S.rho_med = rho_med;
+    S.keep_n = (uint32_t)ceil((double)P.lambda * (double)m);
+    if (S.keep_n > m) S.keep_n = m;
+    atomicAdd(&A.ctr->n_p2, (unsigned long long)m);
+  }
+  __syncthreads();
+  {
+    const float r2ref = S.r2ref, Lref = S.Lref;
+    const float half_alpha = 0.5f * P.alpha;
+    const float c2 = 1.4426950408889634f / (2.0f * P.sigma * P.sigma);
+    for (uint32_t i = tid; i < n1; i += kLeafThreads) {
+      const float r2 = M.r2[i];
+      const float ell = Lref - 1.5f * log2f(__fdiv_rn(r2, r2ref));  // log2(rho_i / sqrt(rho_med^2 + eps))
+      M.wa[i] = half_alpha * ell;
+      M.wc[i] = __fdiv_rn(c2, r2);
+      if (A.use_train) A.train.ell[M.gidx[i]] = ell;
+    }
+  }
+  __syncthreads();
+  // ---- Eq. 15-21: dual-weight gravitational score of every P_2 point
+  {
+    const bool g2 = (P.gamma == 2.0f);
+    const float hg = 0.5f * P.gamma, ek = P.eps_k;
+    for (uint32_t i = tid; i < n1; i += kLeafThreads) {
+      if (!M.flag[i]) continue;
+      const float4 me = M.p1[i];
+      const float ai = M.wa[i], ci = M.wc[i];
+      float F = 0.0f;
+      for (uint32_t t = 0; t < keff; ++t) {
+        const uint32_t j = (uint32_t)nbr[(size_t)i * KMAX + t];
+        const float d2 = sqdist(me, M.p1[j]);
+        const float wt = exp2f(ai + M.wa[j] - d2 * ci);           // w_den * w_dis (Eq. 17, 19)
+        const float D = g2 ? d2 : exp2f(hg * log2f(d2));          // (d^2)^(gamma/2)
+        F += wt / (D + ek);                                       // kernel of Eq. 20
+      }
+      M.F[i] = F;
+    }
+  }
+  __syncthreads();
+  // ---- selection: Top-lambda per leaf by (F desc, input index asc), or ln F >= tau
+  if (P.select_mode == DENOISE_SELECT_TOPRATIO) {
+    for (uint32_t i = tid; i < sn; i += kLeafThreads) {
+      unsigned long long key = kEmpty;
+      if (i < n1 && M.flag[i])
+        key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | __float_as_uint(M.p1[i].w);
+      M.sbuf[i] = key;
+    }
+    __syncthreads();
+    bitonic_sort(M.sbuf, sn);
+    const uint32_t keep_n = S.keep_n;
+    for (uint32_t s = tid; s < m; s += kLeafThreads) {
+      const uint32_t pos = M.por[(uint32_t)(M.sbuf[s] & 0xFFFFFFFFu)];
+      M.flag[pos] = (s < keep_n) ? 2 : 1;
+    }
+  } else {
+    for (uint32_t i = tid; i < n1; i += kLeafThreads)
+      if (M.flag[i]) M.flag[i] = (logf(M.F[i]) >= P.tau) ? 2 : 1;
+  }
+  __syncthreads();
+  // ---- Eq. 22: results in input order
+  const double rho_med = S.rho_med;
+  for (uint32_t i = tid; i < n1; i += kLeafThreads) {
+    const uint32_t g = M.gidx[i];
+    const uint8_t f = M.flag[i];
+    if (f == 0) write_point(A, g, 0, 0.0f, 2);
+    else write_point(A, g, f == 2, M.F[i], f == 2 ? 0 : 3);
+    if (A.use_dbg && A.dbg.leaf_rho_med) A.dbg.leaf_rho_med[g] = rho_med;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// persistent kernel
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf(const LeafArgs A) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long s_mbar;
+  __shared__ LeafShared S;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lmax = A.lmax;
+  LeafMem Ms;
+  carve<uint16_t>(smem, lmax, KMAX, &Ms, (size_t)lmax * 16);
+  float4 *s_pts = (float4 *)smem;
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint32_t n_leaves = A.ctr->n_leaves;
+  uint32_t phase = 0;
+  for (;;) {
+    if (tid == 0) S.leaf = (ld_volatile(&A.ctr->status) & kStFatal) ? 0xFFFFFFFFu : atomicAdd(&A.ctr->leaf_work, 1u);
+    __syncthreads();
+    const uint32_t li = S.leaf;  // block-uniform: one thread decided
+    if (li >= n_leaves) break;
+    const Leaf lf = A.leaves[li];
+    if (lf.count <= lmax) {
+      if (tid == 0) {
+        const uint32_t bytes = lf.count * 16u;
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s_pts);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+            "l"(__cvta_generic_to_global(A.spts + lf.start)), "r"(bytes), "r"(bar)
+            : "memory");
+      }
+      const bool ok = mbar_wait(bar, phase);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(&A.ctr->status, kStTimeout);
+        (void)mbar_wait(bar, phase);  // let the copy in flight land before exiting
+        return;
+      }
+      phase ^= 1u;
+      process_leaf<KMAX, uint16_t>(A, lf, s_pts, Ms, S);
+    } else {
+      LeafMem Mg;
+      carve<uint32_t>(A.big_scratch + (size_t)lf.start * A.big_bpp, lf.count, KMAX, &Mg, 0);
+      process_leaf<KMAX, uint32_t>(A, lf, A.spts + lf.start, Mg, S);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+int leaf_kmax(uint32_t k) { return k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64; }
+
+size_t leaf_smem_bytes(uint32_t lmax, int kmax) {
+  return carve<uint16_t>(nullptr, lmax, kmax, nullptr, (size_t)lmax * 16);
+}
+
+uint32_t leaf_big_bpp(int kmax) {
+  // bound of carve<uint32_t>(cap)/cap for the spill path (cap > 64), alignment
+  // included; a multiple of 16 so that every leaf's area starts 16-byte aligned
+  const uint32_t region_a = (uint32_t)(4 * kmax > 48 ? 4 * kmax : 48);
+  const uint32_t bytes = region_a + 16 + 16 + 6 * 4 + 1 + 16;
+  return (bytes + 15u) & ~15u;
+}
+
+uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit) {
+  uint32_t l = pow2ceil(leaf_capacity < 64 ? 64 : leaf_capacity);
+  while (l > 64 && leaf_smem_bytes(l, kmax) > smem_limit) l >>= 1;
+  return l;
+}
+
+template <int KMAX>
+static int launch_k(const LeafArgs &a, int num_sms, cudaStream_t st) {
+  const size_t smem = leaf_smem_bytes(a.lmax, KMAX);
+  static size_t configured = 0;
+  if (smem > configured) {
+    if (cudaFuncSetAttribute(k_leaf<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return -1;
+    cudaFuncSetAttribute(k_leaf<KMAX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    configured = smem;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf<KMAX>, kLeafThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    return -1;
+  k_leaf<KMAX><<<num_sms * per_sm, kLeafThreads, smem, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st) {
+  switch (leaf_kmax(a.p.k)) {
+    case 8: return launch_k<8>(a, num_sms, st);
+    case 16: return launch_k<16>(a, num_sms, st);
+    case 32: return launch_k<32>(a, num_sms, st);
+    default: return launch_k<64>(a, num_sms, st);
+  }
+}
+
+}  // namespace gd

@@ -1,0 +1,246 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bit-exact: Morton keys, leaf partition, voxel size h, voxel counts, both
+gates, neighbour lists, neighbour distances and r_K^2.  Scores within 1e-5
+relative.  Masks identical except for points whose score is within that
+tolerance of the selection cut (counted, and bounded by the band).
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from gpu_helpers import compare_with_oracle, oracle_params, to_np  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def dn():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_10386_gb300 import Denoiser
+    d = Denoiser(max_points=600_000, max_frames=64)
+    yield d
+    d.close()
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def run_both(dn, orc, xyz, P):
+    g = to_np(dn.run_debug(torch.from_numpy(xyz).cuda(), P))
+    r = orc.denoise(xyz, oracle_params(P), debug=True)
+    return g, r
+
+
+def P_(**kw):
+    from paper_2512_10386_gb300 import Params
+    return Params(**kw)
+
+
+# ---------------------------------------------------------------------------
+# the small object workload (36,750 points, K = 16, leaf capacity 512)
+# ---------------------------------------------------------------------------
+def test_object_workload_full_parity(dn, orc):
+    import synth
+    xyz, _ = synth.object_cloud(seed=0)
+    P = P_(k=16, leaf_capacity=512)
+    g, r = run_both(dn, orc, xyz, P)
+    stats = compare_with_oracle(g, r, P)
+    print("object workload:", stats)
+    assert stats["mismatch"] <= max(4, stats["ambiguous"])
+
+
+@pytest.mark.parametrize("k", [1, 8, 12, 24, 32, 64])
+def test_k_variants(dn, orc, k):
+    import synth
+    xyz, _ = synth.object_cloud(seed=k, n_surface=9000)
+    P = P_(k=k, leaf_capacity=300)
+    g, r = run_both(dn, orc, xyz, P)
+    compare_with_oracle(g, r, P)
+
+
+def test_threshold_mode_and_parameters(dn, orc):
+    import synth
+    xyz, _ = synth.object_cloud(seed=5, n_surface=12000)
+    for kw in (dict(select_mode=1, tau=7.5), dict(alpha=2.0, sigma=0.6, gamma=3.0, select_mode=1, tau=6.0),
+               dict(alpha=-0.5, sigma=1.7, gamma=1.0, eps_k=1e-3, lam=0.7), dict(rho_percentile=10.0, lam=0.9)):
+        P = P_(k=12, **kw)
+        g, r = run_both(dn, orc, xyz, P)
+        compare_with_oracle(g, r, P)
+
+
+@pytest.mark.parametrize("n", [2, 3, 17, 4095, 4096, 4097, 12289])
+def test_ragged_sizes_multi_tile(dn, orc, n):
+    rng = np.random.default_rng(n)
+    xyz = np.concatenate([rng.normal(size=(n - n // 5, 3)) * 0.2,
+                          rng.uniform(-1, 1, size=(n // 5, 3))]).astype(np.float32)
+    P = P_(k=8, leaf_capacity=64, beta=2.0, min_vox_count=2)
+    g, r = run_both(dn, orc, xyz, P)
+    compare_with_oracle(g, r, P)
+
+
+def test_duplicates_and_oversized_leaf(dn, orc):
+    # 2,000 identical points form one max-depth leaf larger than the shared-memory
+    # path: it runs on the global spill area, with every distance tie broken by index
+    rng = np.random.default_rng(1)
+    dup = np.repeat(np.array([[0.25, -0.5, 0.125]], np.float32), 2000, axis=0)
+    rest = rng.uniform(-1, 1, size=(3000, 3)).astype(np.float32)
+    xyz = np.concatenate([rest[:1500], dup, rest[1500:]])
+    P = P_(k=16, leaf_capacity=256)
+    g, r = run_both(dn, orc, xyz, P)
+    assert r["leaf_count"].max() == 2000
+    compare_with_oracle(g, r, P)
+
+
+def test_shallow_octree_large_leaves(dn, orc):
+    import synth
+    xyz, _ = synth.object_cloud(seed=7, n_surface=6000)
+    P = P_(k=16, leaf_capacity=256, max_depth=2)
+    g, r = run_both(dn, orc, xyz, P)
+    assert r["leaf_count"].max() > 256    # above the shared-memory path (capacity 256)
+    compare_with_oracle(g, r, P)
+
+
+def test_max_depth_zero_single_leaf(dn, orc):
+    rng = np.random.default_rng(2)
+    xyz = rng.normal(size=(700, 3)).astype(np.float32)
+    P = P_(k=10, leaf_capacity=8, max_depth=0, min_vox_count=1)
+    g, r = run_both(dn, orc, xyz, P)
+    assert r["n_leaves"] == 1
+    compare_with_oracle(g, r, P)
+
+
+def test_degenerate_clouds(dn, orc):
+    for xyz in (np.zeros((1, 3), np.float32), np.ones((2, 3), np.float32), np.ones((700, 3), np.float32),
+                np.stack([np.arange(300, dtype=np.float32), np.zeros(300, np.float32),
+                          np.zeros(300, np.float32)], 1)):
+        P = P_(k=8, leaf_capacity=64, min_vox_count=1)
+        g, r = run_both(dn, orc, xyz, P)
+        compare_with_oracle(g, r, P)
+
+
+def test_lattice_ties(dn, orc):
+    g1 = np.arange(9, dtype=np.float32) * 0.5
+    xyz = np.stack(np.meshgrid(g1, g1, g1, indexing="ij"), -1).reshape(-1, 3)
+    xyz = xyz[np.random.default_rng(3).permutation(len(xyz))]
+    P = P_(k=8, leaf_capacity=100, min_vox_count=1)
+    g, r = run_both(dn, orc, xyz, P)
+    compare_with_oracle(g, r, P)
+
+
+# ---------------------------------------------------------------------------
+# the dense scan workload at full size (560,000 points, K = 32), as benchmarked
+# ---------------------------------------------------------------------------
+def test_dense_scan_workload_full_parity(dn, orc):
+    import synth
+    xyz, _ = synth.superquadric_scan(seed=1)
+    P = P_(k=32)
+    g, r = run_both(dn, orc, xyz, P)
+    stats = compare_with_oracle(g, r, P)
+    print("dense scan workload:", stats)
+
+
+# ---------------------------------------------------------------------------
+# API behaviour
+# ---------------------------------------------------------------------------
+def test_host_buffers_match_device_buffers(dn):
+    import synth
+    xyz, _ = synth.object_cloud(seed=9, n_surface=5000)
+    P = P_(k=16)
+    rd = dn.run(torch.from_numpy(xyz).cuda(), P)
+    rh = dn.run(torch.from_numpy(xyz).pin_memory(), P)
+    assert rh.mask.device.type == "cpu"
+    assert torch.equal(rd.mask.cpu(), rh.mask) and torch.equal(rd.score.cpu(), rh.score)
+    assert torch.equal(rd.stage.cpu(), rh.stage)
+
+
+def test_deterministic_bytes(dn):
+    import synth
+    xyz, _ = synth.object_cloud(seed=10, n_surface=20000)
+    t = torch.from_numpy(xyz).cuda()
+    a = dn.run(t, P_(k=16))
+    b = dn.run(t, P_(k=16))
+    assert torch.equal(a.mask, b.mask) and torch.equal(a.score, b.score) and torch.equal(a.stage, b.stage)
+
+
+def test_batch_equals_single_frames(dn, orc):
+    import synth
+    frames = [synth.object_cloud(seed=s, n_surface=ns)[0] for s, ns in ((20, 3000), (21, 9000), (22, 1))]
+    frames.insert(1, np.zeros((0, 3), np.float32))
+    offs = np.cumsum([0] + [len(f) for f in frames]).tolist()
+    xyz = np.concatenate(frames)
+    P = P_(k=12)
+    rb = dn.run_batch(torch.from_numpy(xyz).cuda(), offs, P)
+    for f, fr in enumerate(frames):
+        a, b = offs[f], offs[f + 1]
+        if b == a:
+            continue
+        rs = dn.run(torch.from_numpy(fr).cuda(), P)
+        assert torch.equal(rb.mask[a:b], rs.mask) and torch.equal(rb.score[a:b], rs.score)
+        ref = orc.denoise(fr, oracle_params(P), debug=True)
+        compare_with_oracle({"mask": rs.mask.cpu().numpy(), "score": rs.score.cpu().numpy(),
+                             "stage": rs.stage.cpu().numpy()}, ref, P, check_debug=False)
+
+
+def test_graph_mode_matches_direct(dn):
+    import synth
+    xyz, _ = synth.object_cloud(seed=11, n_surface=8000)
+    t = torch.from_numpy(xyz).cuda()
+    ref = dn.run(t, P_(k=16))
+    dn.set_graphs(True)
+    try:
+        for _ in range(3):   # first call captures, the others replay
+            r = dn.run(t, P_(k=16))
+            assert torch.equal(r.mask, ref.mask) and torch.equal(r.score, ref.score)
+        r2 = dn.run(t, P_(k=8))  # new parameters: re-capture
+    finally:
+        dn.set_graphs(False)
+    ref2 = dn.run(t, P_(k=8))
+    assert torch.equal(r2.mask, ref2.mask) and torch.equal(r2.score, ref2.score)
+
+
+def test_errors(dn):
+    from paper_2512_10386_gb300 import _native as N
+    bad = torch.zeros((10, 3), device="cuda")
+    bad[3, 1] = float("nan")
+    with pytest.raises(N.DenoiseError) as e:
+        dn.run(bad, P_())
+    assert e.value.status == N.DENOISE_E_NONFINITE
+    inf = torch.zeros((10, 3), device="cuda")
+    inf[0, 0] = float("inf")
+    with pytest.raises(N.DenoiseError) as e:
+        dn.run(inf, P_())
+    assert e.value.status == N.DENOISE_E_NONFINITE
+    with pytest.raises(N.DenoiseError) as e:
+        dn.run(torch.zeros((10, 3), device="cuda"), P_(k=0))
+    assert e.value.status == N.DENOISE_E_INVAL
+    with pytest.raises(N.DenoiseError) as e:
+        dn.run(torch.zeros((dn.max_points + 1, 3), device="cuda"), P_())
+    assert e.value.status == N.DENOISE_E_CAPACITY
+    r = dn.run(torch.zeros((0, 3), device="cuda"), P_())
+    assert r.mask.numel() == 0
+    # the context stays usable after errors
+    xyz = torch.rand((1000, 3), device="cuda")
+    dn.run(xyz, P_(k=8))
+
+
+def test_stats_count_pairs(dn, orc):
+    import synth
+    xyz, _ = synth.object_cloud(seed=0)
+    P = P_(k=16)
+    dn.run(torch.from_numpy(xyz).cuda(), P)
+    s = dn.stats()
+    r = orc.denoise(xyz, oracle_params(P), debug=True)
+    n1 = r["leaf_n1"].astype(np.int64)
+    assert s["knn_pairs"] == int((n1 * (n1 - 1))[n1 > 1].sum())
+    assert s["n_leaves"] == r["n_leaves"]
+    assert s["n_p1"] == int(n1[n1 > 1].sum())
