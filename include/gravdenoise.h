@@ -183,6 +183,33 @@ int denoise_set_training(denoise_ctx *ctx, int enable);  /* default 0 */
 int denoise_soft_removal(denoise_ctx *ctx, float *removal, void *stream);
 int denoise_backward(denoise_ctx *ctx, const float *grad_removal, double *grad4, void *stream);
 
+/*
+ * No-allocation variant of denoise_run.  The paper has no counterpart: this
+ * call exists for callers that cannot allocate device memory at all -- for
+ * example code that runs under a host framework which owns every device
+ * allocation, or inside a real-time loop whose policy forbids cudaMalloc.
+ * It denoises one cloud of at most DENOISE_NOALLOC_MAX_POINTS points with
+ * exactly the kernels of denoise_run, but all scratch lives in one
+ * file-scope device array of the library (6,505,216 bytes per GPU, held by every
+ * GPU that loads the library until the process exits).  Nothing is allocated:
+ * no context, no cudaMalloc/cudaFree, no pinned memory.
+ *  xyz   [n][3] float32, DEVICE pointer (host pointers are rejected).
+ *  mask, score, stage: as denoise_run, DEVICE pointers or NULL.
+ *  Works on the calling thread's current CUDA device.  The first call on a
+ *  device looks up the scratch array's device address (cudaGetSymbolAddress);
+ *  make that first call before any stream capture.  Each call synchronises
+ *  `stream` and returns the device-side status.
+ *  All calls share the one scratch array, and it keeps the last call's
+ *  contents (the call clears what must start at zero): calls that overlap on
+ *  the GPU -- from two host threads, or on two streams -- race and must not
+ *  be made.
+ * Errors: E_INVAL (NULL or host xyz/outputs, bad parameters), E_CAPACITY
+ * (n > DENOISE_NOALLOC_MAX_POINTS), E_NONFINITE, E_TIMEOUT, E_CUDA.
+ */
+#define DENOISE_NOALLOC_MAX_POINTS 16384u
+int denoise_run_noalloc(const float *xyz, size_t n, const denoise_params *p, uint8_t *mask, float *score,
+                        uint8_t *stage, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

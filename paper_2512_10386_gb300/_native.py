@@ -31,8 +31,9 @@ EXPORTED = [
     "denoise_create", "denoise_destroy", "denoise_strerror", "denoise_run", "denoise_run_batch",
     "denoise_set_sync", "denoise_set_graphs", "denoise_set_profiling", "denoise_get_status",
     "denoise_get_stats", "denoise_run_debug", "denoise_set_training", "denoise_soft_removal",
-    "denoise_backward",
+    "denoise_backward", "denoise_run_noalloc",
 ]
+DENOISE_NOALLOC_MAX_POINTS = 16384
 
 
 class denoise_params(ctypes.Structure):
@@ -105,6 +106,7 @@ def lib():
     L.denoise_get_stats.argtypes = [_V, ctypes.POINTER(denoise_stats)]
     L.denoise_soft_removal.argtypes = [_V, _V, _V]
     L.denoise_backward.argtypes = [_V, _V, ctypes.POINTER(ctypes.c_double), _V]
+    L.denoise_run_noalloc.argtypes = [_V, ctypes.c_size_t, _P, _V, _V, _V, _V]
     for name in EXPORTED:
         if name != "denoise_strerror":
             getattr(L, name).restype = ctypes.c_int
@@ -184,6 +186,10 @@ def denoise_get_stats(ctx) -> denoise_stats:
 
 def denoise_soft_removal(ctx, removal_ptr, stream) -> int:
     return lib().denoise_soft_removal(ctx, removal_ptr, stream)
+
+
+def denoise_run_noalloc(xyz_ptr, n, params: denoise_params, mask_ptr, score_ptr, stage_ptr, stream) -> int:
+    return lib().denoise_run_noalloc(xyz_ptr, n, ctypes.byref(params), mask_ptr, score_ptr, stage_ptr, stream)
 
 
 def denoise_backward(ctx, grad_ptr, stream):
