@@ -55,6 +55,22 @@ def _dist():
     return rank, world, local
 
 
+def rank_seed(rank: int) -> int:
+    """Weak scaling: each rank denoises its own cloud (seed 1 + rank)."""
+    return 1 + rank
+
+
+def max_over_ranks(value: float, device: str) -> float:
+    """The slowest rank's time, on every rank (the job's time)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -146,7 +162,7 @@ def _profile_traffic():
 
 def _workload(rank: int):
     import synth
-    return synth.superquadric_scan(seed=1 + rank)
+    return synth.superquadric_scan(seed=rank_seed(rank))
 
 
 def _oracle_crop(xyz, frac=0.125):
@@ -234,6 +250,7 @@ def run_ours(args):
     out = d.run(xyz, P, stream=stream)
     torch.cuda.synchronize()
 
+    clocks = ClockSampler(local).__enter__()   # sampled from warm-up to the end of the GPU sections
     d.set_profiling(True)
     for _ in range(args.warmup):
         d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
@@ -243,25 +260,21 @@ def run_ours(args):
     step_ms, leaf_ms = [], []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches = 0
-    with ClockSampler(local) as clocks:
-        torch.cuda.synchronize()
-        for s in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(s))
-                ev[s][0].record(stream)
-            d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
-            ev[s][1].record(stream)
-            st = d.stats()
-            launches += st["launches"]
-            leaf_ms.append(st["stage_ms"][3])
-        torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+        d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
+        ev[s][1].record(stream)
+        st = d.stats()
+        launches += st["launches"]
+        leaf_ms.append(st["stage_ms"][3])
+    torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     stats = d.stats()
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), "cuda")
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     value = n * world * args.steps / (total_ms / 1000.0)
 
@@ -298,11 +311,7 @@ def run_ours(args):
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    e2e_total = sum(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_ms), "cuda")
     e2e = {"value": n * world * args.steps / (e2e_total / 1000.0), "unit": UNIT,
            "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 6 * n,
            "ms_per_step": e2e_total / args.steps}
@@ -323,11 +332,20 @@ def run_ours(args):
     d.set_graphs(False)
     graph = {"value": n * args.steps / (sum(g_ms) / 1000.0), "unit": UNIT,
              "ms_per_step": sum(g_ms) / args.steps}
+    # keep the GPU busy on the same step for ~1 s so the clock sampler sees load
+    t_end = time.perf_counter() + 1.0
+    while time.perf_counter() < t_end:
+        d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
+    torch.cuda.synchronize()
+    clocks.__exit__(None, None, None)
     d.close()
 
     batched = None
     if not args.no_batch:
         batched = run_batched(args, stream, flush)
+    serving = None
+    if args.serving_frames > 0 and rank == 0:
+        serving = run_serving(args)
 
     if rank != 0:
         if dist:
@@ -344,6 +362,7 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "ms_per_frame": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
         "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "graph_replay": graph, "batched": batched,
+        "serving": serving,
         "clocks": clocks.summary(), "gpu_launches": launches,
         "stats": {k: stats[k] for k in ("n_leaves", "knn_pairs", "n_p1", "n_p2", "launches")},
     }
@@ -413,6 +432,38 @@ def run_batched(args, stream, flush):
     }
 
 
+def run_serving(args):
+    """The serving workload, shortened: a Poisson 20 Hz stream (seed 7) mixing dense
+    128-beam frames (~1.0 M points, 10 % outliers) and 32-beam frames (~100 k,
+    15 % snow), played in real time through the continuous-batching server; then
+    the same frames all at once (throughput mode)."""
+    import synth
+    from paper_2512_10386_gb300 import Params
+    from paper_2512_10386_gb300.serving import Request, Server, latency_report
+    stream = synth.serving_stream(seed=7, n_frames=args.serving_frames)
+    reqs = []
+    for r in stream.requests:
+        xyz, _ = stream.frame(r)
+        reqs.append(Request(len(reqs), r.t_arrival, xyz, r.kind))
+    dense = max(len(q.xyz) for q in reqs)
+    P = Params(k=24)
+    srv = Server(P, capacities=[dense, dense, 4 * 130_000, 4 * 130_000], max_frames=4)
+    try:
+        srv.serve(reqs[:4], realtime=False)  # warm-up: first launches, module loading
+        for r, src in zip(reqs, stream.requests):
+            r.t_arrival = src.t_arrival
+        t0 = time.perf_counter()
+        comps = srv.serve(reqs, realtime=True)
+        live = latency_report(comps, time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        comps = srv.serve(reqs, realtime=False)
+        burst = latency_report(comps, time.perf_counter() - t0)
+    finally:
+        srv.close()
+    return {"workload": f"{len(reqs)} frames, Poisson 20 Hz, seed 7, dense ~1.0M / sparse ~100k mix, K=24",
+            "realtime": live, "all_at_once": burst}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -422,6 +473,7 @@ def main():
     ap.add_argument("--frames", type=int, default=64)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serving-frames", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

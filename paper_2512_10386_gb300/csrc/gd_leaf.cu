@@ -4,9 +4,9 @@
 // leaf at a time, every per-leaf step of Sec. 3 in shared memory:
 //   extents and adaptive voxel size h (Eq. 10-11) -> voxel occupancy counts in a
 //   shared hash table with warp-aggregated atomics, voxel gate (Eq. 12) and
-//   compaction of P_1 -> tie ranks (input-index order) by bitonic sort -> kNN of
-//   every P_1 point against the leaf's P_1 (register top-K, candidates
-//   broadcast from shared memory), r_K (Eq. 13) -> exact percentile gate
+//   compaction of P_1 -> kNN of every P_1 point against the leaf's P_1 (seeded
+//   register top-K, candidates broadcast from shared memory, ties broken by
+//   input index), r_K (Eq. 13) -> exact percentile gate
 //   (Eq. 14) as a rank cut on r_K^2 -> median density (Eq. 16) -> dual-weight
 //   gravitational score (Eq. 15-21) -> Top-lambda or log-threshold selection,
 //   scattered to input order (Eq. 22).
@@ -26,6 +26,9 @@ constexpr int kLeafThreads = 128;
 constexpr int kLeafWarps = kLeafThreads / 32;
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned long long kInvalid = ~0ull - 1ull;
+constexpr uint32_t kPend = 4;  // parked kNN candidates per lane before a warp-wide merge
+// the sort buffer also holds the parked candidates during the kNN
+constexpr size_t kPendBytes = (size_t)kPend * kLeafThreads * sizeof(float);
 
 __host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 __host__ __device__ __forceinline__ uint32_t pow2ceil(uint32_t x) {
@@ -36,16 +39,15 @@ __host__ __device__ __forceinline__ uint32_t pow2ceil(uint32_t x) {
 
 // Per-leaf working arrays: shared memory (small leaves) or global spill (large).
 struct LeafMem {
-  float4 *p1;                // [cap] P_1 points; w = input index, then tie rank
+  float4 *p1;                // [cap] P_1 points; w = input index (bits)
   unsigned long long *hkey;  // [hcap] voxel hash keys
   uint32_t *hcnt;            // [hcap] voxel occupancy
   unsigned long long *sbuf;  // [scap] sort buffer
   float *r2, *wa, *wc, *F;   // [cap] per P_1 position
   uint32_t *gidx;            // [cap] global input index per P_1 position
-  uint32_t *por;             // [cap] P_1 position of each tie rank
   uint8_t *flag;             // [cap] 0 removed by density gate, 1 scored, 2 kept
-  void *nbr;                 // [cap][KMAX] neighbour positions
-  uint32_t hcap, scap;
+  void *nbr;                 // [KMAX][cap] neighbour positions (transposed: rank-major)
+  uint32_t hcap, scap, cap;
 };
 
 // Layout of the per-leaf arrays.  `alias_head` bytes at the start (the TMA
@@ -67,12 +69,14 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
     m->nbr = (void *)base;
     m->hcap = hcap;
     m->scap = scap;
+    m->cap = cap;
   }
   size_t o = off;
   auto take = [&](size_t bytes) { size_t r = o; o = al16(o + bytes); return r; };
-  const size_t p1 = take((size_t)cap * 16), sb = take((size_t)scap * 8);
+  const size_t sbytes = (size_t)scap * 8 > kPendBytes ? (size_t)scap * 8 : kPendBytes;
+  const size_t p1 = take((size_t)cap * 16), sb = take(sbytes);
   const size_t r2 = take((size_t)cap * 4), wa = take((size_t)cap * 4), wc = take((size_t)cap * 4);
-  const size_t F = take((size_t)cap * 4), gi = take((size_t)cap * 4), po = take((size_t)cap * 4);
+  const size_t F = take((size_t)cap * 4), gi = take((size_t)cap * 4);
   const size_t fl = take((size_t)cap);
   if (m) {
     m->p1 = (float4 *)(base + p1);
@@ -82,7 +86,6 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
     m->wc = (float *)(base + wc);
     m->F = (float *)(base + F);
     m->gidx = (uint32_t *)(base + gi);
-    m->por = (uint32_t *)(base + po);
     m->flag = (uint8_t *)(base + fl);
   }
   return o;
@@ -175,6 +178,25 @@ __device__ void bitonic_sort(unsigned long long *a, uint32_t n) {
   }
 }
 
+__device__ void bitonic_sort_u32(uint32_t *a, uint32_t n) {
+  for (uint32_t k = 2; k <= n; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < n; i += kLeafThreads) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const uint32_t x = a[i], y = a[l];
+          const bool asc = (i & k) == 0;
+          if ((x > y) == asc) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // squared distance with the fixed FP32 operation order of the method's reading:
 // dx = x_j - x_i;  d^2 = fma(dz, dz, fma(dy, dy, dx*dx))
 __device__ __forceinline__ float sqdist(const float4 &a, const float4 &b) {
@@ -185,17 +207,65 @@ __device__ __forceinline__ float sqdist(const float4 &a, const float4 &b) {
 // Sorted register lists (ascending); insert c and drop the largest:
 // L'[s] = min(L[s], max(L[s-1], c)), L'[0] = min(L[0], c).  Every slot uses the
 // old neighbour value, so the KMAX updates are independent (no serial chain).
+// ---------------------------------------------------------------------------
+// per-thread sorted register lists (all indices compile-time)
+// ---------------------------------------------------------------------------
+// insert c, dropping the largest: L'[s] = min(L[s], max(L[s-1], c)), L'[0] =
+// min(L[0], c); every slot reads old values, so the KMAX updates are independent
 template <int KMAX>
-__device__ __forceinline__ void topk_insert_f(float (&L)[KMAX], float c) {
+__device__ __forceinline__ void topk_insert(unsigned long long (&L)[KMAX], unsigned long long c) {
 #pragma unroll
-  for (int s = KMAX - 1; s > 0; --s) L[s] = fminf(L[s], fmaxf(L[s - 1], c));
-  L[0] = fminf(L[0], c);
+  for (int s = KMAX - 1; s > 0; --s) {
+    const unsigned long long m = L[s - 1] > c ? L[s - 1] : c;
+    L[s] = L[s] < m ? L[s] : m;
+  }
+  L[0] = L[0] < c ? L[0] : c;
 }
-template <int KMAX>
-__device__ __forceinline__ void topk_insert_u(uint32_t (&L)[KMAX], uint32_t c) {
+
+// ascending bitonic sort
+template <int N>
+__device__ __forceinline__ void regsort_f(float (&L)[N]) {
 #pragma unroll
-  for (int s = KMAX - 1; s > 0; --s) L[s] = min(L[s], max(L[s - 1], c));
-  L[0] = min(L[0], c);
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const float a = L[i], b = L[l];
+          const bool asc = (i & k) == 0;
+          L[i] = asc ? fminf(a, b) : fmaxf(a, b);
+          L[l] = asc ? fmaxf(a, b) : fminf(a, b);
+        }
+      }
+    }
+  }
+}
+
+// Merge the lane's np (<= kPend) parked values (column `tid` of `pend`) into the
+// ascending list L: sort them (padded with +inf), take min(L[KMAX-kPend+i],
+// B[kPend-1-i]) (a bitonic sequence holding the KMAX smallest), then restore the
+// order with a half-cleaner cascade.
+template <int KMAX>
+__device__ __forceinline__ void merge_pending(float (&L)[KMAX], const float *pend, uint32_t np, uint32_t tid) {
+  float B[kPend];
+#pragma unroll
+  for (int i = 0; i < (int)kPend; ++i) B[i] = ((uint32_t)i < np) ? pend[i * kLeafThreads + tid] : INFINITY;
+  regsort_f<kPend>(B);
+#pragma unroll
+  for (int i = 0; i < (int)kPend; ++i) L[KMAX - kPend + i] = fminf(L[KMAX - kPend + i], B[kPend - 1 - i]);
+#pragma unroll
+  for (int j = KMAX / 2; j > 0; j >>= 1) {
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+      if ((i & j) == 0) {
+        const float a = L[i], b = L[i + j];
+        L[i] = fminf(a, b);
+        L[i + j] = fmaxf(a, b);
+      }
+    }
+  }
 }
 
 __device__ __forceinline__ void write_point(const LeafArgs &A, uint32_t g, uint8_t mk, float sc, uint8_t st) {
@@ -352,140 +422,189 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     atomicAdd(&A.ctr->knn_pairs, (unsigned long long)n1 * (unsigned long long)(n1 - 1));
     atomicAdd(&A.ctr->n_p1, (unsigned long long)n1);
   }
-  // ---- tie ranks: order of input index among P_1
   const uint32_t sn = pow2ceil(n1);
-  for (uint32_t i = tid; i < sn; i += kLeafThreads)
-    M.sbuf[i] = (i < n1) ? (((unsigned long long)M.gidx[i] << 32) | i) : kEmpty;
-  __syncthreads();
-  bitonic_sort(M.sbuf, sn);
-  for (uint32_t r = tid; r < n1; r += kLeafThreads) {
-    const uint32_t pos = (uint32_t)(M.sbuf[r] & 0xFFFFFFFFu);
-    M.por[r] = pos;
-    M.p1[pos].w = __uint_as_float(r);
-  }
-  __syncthreads();
 
-  // ---- kNN on P_1 (excluding self), order by (d^2, input index).
-  // Phase A: the k_eff-th smallest d^2, theta, with a register min/max network on
-  // FP32 values only (placeholders -1 fill the unused KMAX - k_eff slots).
-  // Phase B: a second scan keeps every candidate with d^2 < theta and, among the
-  // candidates at exactly theta, the ones with the smallest input-index ranks.
-  // The set is the k_eff smallest by (d^2, input index), as with a full sort.
-  const float delta2 = __fmul_rn(S.delta, S.delta);
-  for (uint32_t qb = 0; qb < n1; qb += kLeafThreads) {
-    const uint32_t q = qb + tid;
-    if (q < n1) {
-      const float4 me = M.p1[q];
-      const uint32_t j0 = qb + w * 32;  // start near the warp's own queries (spatially local)
+  // ---- kNN on P_1 (excluding self), order by (d^2, input index): one thread per query.
+  // Phase A finds theta, the k_eff-th smallest d^2, in a sorted register list of
+  // FP32 values (placeholders -1 fill the unused KMAX - k_eff slots).  The list
+  // is seeded with the k_eff Morton-order neighbours of the query (window
+  // [ws, we]) and sorted once by a register bitonic network.  The scan then
+  // broadcasts every other candidate from shared memory to the warp; a lane
+  // whose candidate beats its current k-th value parks it in its column of a
+  // small shared buffer, and when any lane has kPend parked values the warp
+  // merges them into the lists (sort of kPend values + bitonic merge), so the
+  // list update is paid once per batch rather than once per insertion.
+  // Phase B rescans all candidates: every d^2 < theta is kept and, among the
+  // candidates at exactly theta, those with the smallest input index.  The set
+  // is the k_eff smallest by (d^2, input index), as with a full sort.
+  {
+    // parked candidates live in the sort buffer, idle during the kNN (kPend columns of kLeafThreads)
+    float *const pend = reinterpret_cast<float *>(M.sbuf);
+    const float delta2 = __fmul_rn(S.delta, S.delta);
+    const uint32_t cap = M.cap;
+    const bool dbg_n = A.use_dbg && A.dbg.nbr, dbg_d = A.use_dbg && A.dbg.nbr_d2;
+    for (uint32_t qb = 0; qb < n1; qb += kLeafThreads) {
+      const uint32_t q = qb + tid;
+      const bool act = q < n1;
+      if (!__any_sync(0xFFFFFFFFu, act)) continue;  // whole warp idle (warp-uniform)
+      const uint32_t qq = act ? q : n1 - 1;          // idle lanes shadow a real query, results discarded
+      const float4 me = M.p1[qq];
+      const uint32_t j0 = qb + w * 32;               // < n1: lane 0 of a busy warp is busy
+      const uint32_t half = keff / 2;
+      uint32_t ws = (qq > half) ? qq - half : 0u;
+      if (ws > n1 - 1 - keff) ws = n1 - 1 - keff;
+      const uint32_t we = ws + keff;
       float L[KMAX];
 #pragma unroll
-      for (int s = 0; s < KMAX; ++s) L[s] = (s < KMAX - (int)keff) ? -1.0f : INFINITY;
-      for (uint32_t j = j0, c = 0; c < n1; ++c, j = (j + 1 == n1) ? 0 : j + 1) {
-        if (j == q) continue;
-        const float d2 = sqdist(me, M.p1[j]);
-        if (d2 < L[KMAX - 1]) topk_insert_f<KMAX>(L, d2);
+      for (int sl = 0; sl < KMAX; ++sl) {
+        const int r = sl - (KMAX - (int)keff);
+        float v = -1.0f;
+        if (r >= 0) {
+          uint32_t j = ws + (uint32_t)r;
+          if (j >= qq) ++j;
+          v = sqdist(me, M.p1[j]);
+        }
+        L[sl] = v;
       }
+      regsort_f<KMAX>(L);
+      uint32_t np = 0;
+      for (uint32_t pass = 0; pass < 2; ++pass) {
+        const uint32_t jb = pass == 0 ? j0 : 0u, je = pass == 0 ? n1 : j0;
+        for (uint32_t j = jb; j < je; ++j) {
+          const float d2 = sqdist(me, M.p1[j]);
+          if (d2 < L[KMAX - 1] && (j < ws || j > we)) {
+            pend[np * kLeafThreads + tid] = d2;
+            ++np;
+          }
+          if (__any_sync(0xFFFFFFFFu, np == kPend)) {
+            merge_pending<KMAX>(L, pend, np, tid);
+            np = 0;
+          }
+        }
+      }
+      merge_pending<KMAX>(L, pend, np, tid);
       const float theta = L[KMAX - 1];
       uint32_t below = 0;
 #pragma unroll
-      for (int s = 0; s < KMAX; ++s) below += (L[s] >= 0.0f && L[s] < theta) ? 1u : 0u;
+      for (int sl = 0; sl < KMAX; ++sl) below += (L[sl] >= 0.0f && L[sl] < theta) ? 1u : 0u;
       const uint32_t ties_needed = keff - below;
-      uint32_t T[KMAX];
+      unsigned long long T[KMAX];  // ties at theta: (input index, position), ascending
 #pragma unroll
-      for (int s = 0; s < KMAX; ++s) T[s] = 0xFFFFFFFFu;
-      const uint32_t gq = M.gidx[q];
-      const bool dbg_n = A.use_dbg && A.dbg.nbr, dbg_d = A.use_dbg && A.dbg.nbr_d2;
+      for (int sl = 0; sl < KMAX; ++sl) T[sl] = kEmpty;
+      const uint32_t gq = M.gidx[qq];
       uint32_t a = 0;
-      for (uint32_t j = j0, c = 0; c < n1; ++c, j = (j + 1 == n1) ? 0 : j + 1) {
-        if (j == q) continue;
+      for (uint32_t j = 0; j < n1; ++j) {
         const float4 cj = M.p1[j];
         const float d2 = sqdist(me, cj);
+        if (j == qq) continue;
         if (d2 < theta) {
-          if (a < keff) {
-            nbr[(size_t)q * KMAX + a] = (IdxT)j;
-            if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + a] = M.gidx[j];
+          if (act && a < keff) {
+            nbr[(size_t)a * cap + qq] = (IdxT)j;
+            if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + a] = __float_as_uint(cj.w);
             if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + a] = d2;
             if (A.use_train) {
-              A.train.nbr[(size_t)gq * P.k + a] = M.gidx[j];
+              A.train.nbr[(size_t)gq * P.k + a] = __float_as_uint(cj.w);
               A.train.nd2[(size_t)gq * P.k + a] = d2;
             }
           }
           ++a;
         } else if (d2 == theta) {
-          const uint32_t rk = __float_as_uint(cj.w);
-          if (rk < T[KMAX - 1]) topk_insert_u<KMAX>(T, rk);
+          const unsigned long long key = ((unsigned long long)__float_as_uint(cj.w) << 32) | j;
+          if (key < T[KMAX - 1]) topk_insert<KMAX>(T, key);
         }
       }
-      if (a != below) atomicOr(&A.ctr->status, kStInternal);  // the two scans must agree
+      if (act) {
+        if (a != below) atomicOr(&A.ctr->status, kStInternal);  // the two phases must agree
 #pragma unroll
-      for (int s = 0; s < KMAX; ++s) {
-        if ((uint32_t)s < ties_needed && below + s < keff) {
-          const uint32_t t = below + s;
-          const uint32_t npos = (T[s] < n1) ? M.por[T[s]] : 0u;
-          nbr[(size_t)q * KMAX + t] = (IdxT)npos;
-          if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = M.gidx[npos];
-          if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = theta;
-          if (A.use_train) {
-            A.train.nbr[(size_t)gq * P.k + t] = M.gidx[npos];
-            A.train.nd2[(size_t)gq * P.k + t] = theta;
+        for (int sl = 0; sl < KMAX; ++sl) {
+          if ((uint32_t)sl < ties_needed && below + sl < keff && T[sl] != kEmpty) {
+            const uint32_t t = below + sl;
+            const uint32_t npos = (uint32_t)(T[sl] & 0xFFFFFFFFu);
+            const uint32_t g = (uint32_t)(T[sl] >> 32);
+            nbr[(size_t)t * cap + qq] = (IdxT)npos;
+            if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = g;
+            if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = theta;
+            if (A.use_train) {
+              A.train.nbr[(size_t)gq * P.k + t] = g;
+              A.train.nd2[(size_t)gq * P.k + t] = theta;
+            }
           }
         }
-      }
-      for (uint32_t t = keff; t < P.k; ++t) {
-        if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
-        if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = 0.0f;
-        if (A.use_train) {
-          A.train.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
-          A.train.nd2[(size_t)gq * P.k + t] = 0.0f;
+        for (uint32_t t = keff; t < P.k; ++t) {
+          if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
+          if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = 0.0f;
+          if (A.use_train) {
+            A.train.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
+            A.train.nd2[(size_t)gq * P.k + t] = 0.0f;
+          }
         }
+        const float rt = (theta < delta2) ? delta2 : theta;
+        M.r2[qq] = rt;
+        if (A.use_dbg && A.dbg.r2) A.dbg.r2[gq] = rt;
+        if (A.use_train) A.train.r2[gq] = rt;
       }
-      const float rt = (theta < delta2) ? delta2 : theta;
-      M.r2[q] = rt;
-      if (A.use_dbg && A.dbg.r2) A.dbg.r2[gq] = rt;
-      if (A.use_train) A.train.r2[gq] = rt;
     }
   }
   __syncthreads();
 
   // ---- Eq. 14: exact percentile cut, as a rank cut on r_K^2 (rho decreasing in r_K)
-  for (uint32_t i = tid; i < sn; i += kLeafThreads)
-    M.sbuf[i] = (i < n1) ? (((unsigned long long)__float_as_uint(M.r2[i]) << 32) | i) : kEmpty;
+  uint32_t *const vbuf = reinterpret_cast<uint32_t *>(M.sbuf);
+  for (uint32_t i = tid; i < sn; i += kLeafThreads) vbuf[i] = (i < n1) ? __float_as_uint(M.r2[i]) : 0xFFFFFFFFu;
   __syncthreads();
-  bitonic_sort(M.sbuf, sn);
+  bitonic_sort_u32(vbuf, sn);
   if (tid == 0) {
     const double pos = __dadd_rn(__ddiv_rn(__dmul_rn((double)n1, (double)P.rho_percentile), 100.0), 0.5);
     const double cc = ceil(pos);
     const uint32_t c = (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;
-    S.Rbits = (uint32_t)(M.sbuf[n1 - c] >> 32);
+    S.Rbits = vbuf[n1 - c];
   }
   __syncthreads();
   const uint32_t Rb = S.Rbits;
   for (uint32_t i = tid; i < n1; i += kLeafThreads) {
-    const uint32_t v = (uint32_t)(M.sbuf[i] >> 32);
-    if (v <= Rb && (i + 1 == n1 || (uint32_t)(M.sbuf[i + 1] >> 32) > Rb)) S.m = i + 1;
+    const uint32_t v = vbuf[i];
+    if (v <= Rb && (i + 1 == n1 || vbuf[i + 1] > Rb)) S.m = i + 1;
     M.flag[i] = (__float_as_uint(M.r2[i]) <= Rb) ? 1 : 0;
   }
   __syncthreads();
   const uint32_t m = S.m;
-  // ---- Eq. 16: median density over P_2; per-leaf constants in FP64
+  // ---- Eq. 16: median density over P_2 and the per-leaf constants of the score.
+  // With rho(r2) = k_eff / (4/3 pi r2^1.5), the score needs
+  // ell_i = log2(rho_i / sqrt(rho_med^2 + eps_rho)) = Lref - 1.5 log2(r2_i / r2ref)
+  // with r2ref the lower-middle r2 of P_2 and Lref = log2(rho(r2ref)) -
+  // log2(rho_med) - 0.5 log2(1 + eps_rho / rho_med^2).  Every term is a log2 of a
+  // ratio near 1 (or the eps correction), evaluated in FP32 without overflow.
   if (tid == 0) {
-    const double k43pi = (4.0 / 3.0) * 3.14159265358979323846;
-    auto rho_of = [&](uint32_t bits) {
-      const double rr = (double)__uint_as_float(bits);
-      return (double)keff / __dmul_rn(k43pi, __dmul_rn(rr, sqrt(rr)));
-    };
     const uint32_t mid = (m - 1) / 2;
-    double rho_med;
-    if (m & 1u) rho_med = rho_of((uint32_t)(M.sbuf[mid] >> 32));
-    else rho_med = 0.5 * (rho_of((uint32_t)(M.sbuf[m / 2 - 1] >> 32)) + rho_of((uint32_t)(M.sbuf[m / 2] >> 32)));
-    const double D2 = __dadd_rn(__dmul_rn(rho_med, rho_med), (double)P.eps_rho);
-    const uint32_t refb = (uint32_t)(M.sbuf[mid] >> 32);
-    S.r2ref = __uint_as_float(refb);
-    S.Lref = (float)(log2(rho_of(refb)) - 0.5 * log2(D2));
-    S.rho_med = rho_med;
+    const float ra = __uint_as_float(vbuf[mid]);
+    // log2(rho(ra) / rho_med): 0 for odd m, 1 - log2(1 + (ra / rb)^1.5) for even m
+    float lr = 0.0f;
+    float rb = ra;
+    if (!(m & 1u)) {
+      rb = __uint_as_float(vbuf[m / 2]);
+      const float t = __fdiv_rn(ra, rb);
+      lr = 1.0f - log2f(1.0f + t * sqrtf(t));
+    }
+    // log2(rho_med) = log2(rho(ra)) - lr, with log2(rho(ra)) = log2(k_eff) - log2(4/3 pi) - 1.5 log2(ra)
+    const float l_rho_a = log2f((float)keff) - 2.0665336287511624f - 1.5f * log2f(ra);
+    const float l_med = l_rho_a - lr;
+    float corr = 0.0f;
+    if (P.eps_rho > 0.0f) {
+      const float lx = log2f(P.eps_rho) - 2.0f * l_med;  // log2(eps_rho / rho_med^2)
+      corr = (lx > 100.0f) ? 0.5f * lx : 0.5f * log2f(1.0f + exp2f(lx));
+    }
+    S.r2ref = ra;
+    S.Lref = lr - corr;
     S.keep_n = (uint32_t)ceil((double)P.lambda * (double)m);
     if (S.keep_n > m) S.keep_n = m;
     atomicAdd(&A.ctr->n_p2, (unsigned long long)m);
+    if (A.use_dbg && A.dbg.leaf_rho_med) {  // exact FP64 value for the parity output only
+      const double k43pi = (4.0 / 3.0) * 3.14159265358979323846;
+      auto rho_of = [&](float r2) {
+        const double rr = (double)r2;
+        return (double)keff / __dmul_rn(k43pi, __dmul_rn(rr, sqrt(rr)));
+      };
+      S.rho_med = (m & 1u) ? rho_of(ra) : 0.5 * (rho_of(__uint_as_float(vbuf[m / 2 - 1])) + rho_of(rb));
+    }
   }
   __syncthreads();
   {
@@ -511,7 +630,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       const float ai = M.wa[i], ci = M.wc[i];
       float F = 0.0f;
       for (uint32_t t = 0; t < keff; ++t) {
-        const uint32_t j = (uint32_t)nbr[(size_t)i * KMAX + t];
+        const uint32_t j = (uint32_t)nbr[(size_t)t * M.cap + i];
         const float d2 = sqdist(me, M.p1[j]);
         const float wt = exp2f(ai + M.wa[j] - d2 * ci);           // w_den * w_dis (Eq. 17, 19)
         const float D = g2 ? d2 : exp2f(hg * log2f(d2));          // (d^2)^(gamma/2)
@@ -521,20 +640,23 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     }
   }
   __syncthreads();
-  // ---- selection: Top-lambda per leaf by (F desc, input index asc), or ln F >= tau
+  // ---- selection: Top-lambda per leaf by (F desc, input index asc), or ln F >= tau.
+  // Top-lambda: sort the keys (~F, input index); a point is kept iff its own key
+  // is at most the keep_n-th smallest key (keys are unique).
   if (P.select_mode == DENOISE_SELECT_TOPRATIO) {
     for (uint32_t i = tid; i < sn; i += kLeafThreads) {
       unsigned long long key = kEmpty;
       if (i < n1 && M.flag[i])
-        key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | __float_as_uint(M.p1[i].w);
+        key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | M.gidx[i];
       M.sbuf[i] = key;
     }
     __syncthreads();
     bitonic_sort(M.sbuf, sn);
-    const uint32_t keep_n = S.keep_n;
-    for (uint32_t s = tid; s < m; s += kLeafThreads) {
-      const uint32_t pos = M.por[(uint32_t)(M.sbuf[s] & 0xFFFFFFFFu)];
-      M.flag[pos] = (s < keep_n) ? 2 : 1;
+    const unsigned long long cut = M.sbuf[S.keep_n - 1];
+    for (uint32_t i = tid; i < n1; i += kLeafThreads) {
+      if (!M.flag[i]) continue;
+      const unsigned long long key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | M.gidx[i];
+      M.flag[i] = (key <= cut) ? 2 : 1;
     }
   } else {
     for (uint32_t i = tid; i < n1; i += kLeafThreads)
@@ -630,11 +752,21 @@ size_t leaf_smem_bytes(uint32_t lmax, int kmax) {
 }
 
 uint32_t leaf_big_bpp(int kmax) {
-  // bound of carve<uint32_t>(cap)/cap for the spill path (cap > 64), alignment
-  // included; a multiple of 16 so that every leaf's area starts 16-byte aligned
-  const uint32_t region_a = (uint32_t)(4 * kmax > 48 ? 4 * kmax : 48);
-  const uint32_t bytes = region_a + 16 + 16 + 6 * 4 + 1 + 16;
-  return (bytes + 15u) & ~15u;
+  // max over spill-path leaf sizes (cap > 64) of carve<uint32_t>(cap)/cap, rounded
+  // up to a multiple of 16 so that every leaf's area starts 16-byte aligned.  The
+  // ratio is largest for small caps (fixed-size parts); beyond 2^16 points it only
+  // falls, so scanning 65..65536 bounds every size.
+  static uint32_t cached[65] = {0};
+  if (kmax <= 64 && cached[kmax]) return cached[kmax];
+  size_t worst = 0;
+  for (uint32_t cap = 65; cap <= 65536; ++cap) {
+    const size_t b = carve<uint32_t>(nullptr, cap, kmax, nullptr, 0);
+    const size_t per = (b + cap - 1) / cap;
+    if (per > worst) worst = per;
+  }
+  const uint32_t bpp = (uint32_t)((worst + 15) & ~size_t(15));
+  if (kmax <= 64) cached[kmax] = bpp;
+  return bpp;
 }
 
 uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit) {
