@@ -373,18 +373,26 @@ def run_ours(args):
 
 
 def run_batched(args, stream, flush):
-    """64 LiDAR frames of 60k-130k points: one graph-captured batch vs one call per frame."""
+    """64 LiDAR frames of 60k-130k points (K = 24): the autotuner picks the leaf
+    capacity and the leaf kernel's CTAs per SM for the graph-captured batch; the
+    batch is then timed against the same frames one call each, at the tuned
+    capacity (identical masks required)."""
+    import dataclasses
+
     import torch
 
     import synth
     from paper_2512_10386_gb300 import Denoiser, Params
+    from paper_2512_10386_gb300.autotune import tune_batch
     frames = synth.lidar_batch(n_frames=args.frames)
     sizes = [len(f[0]) for f in frames]
     offs = np.cumsum([0] + sizes).tolist()
     xyz = torch.from_numpy(np.concatenate([f[0] for f in frames])).cuda()
     total = int(offs[-1])
-    P = Params(k=24)
     d = Denoiser(max_points=total, max_frames=len(frames))
+    tuned = tune_batch(xyz, offs, Params(k=24), reps=3, denoiser=d)
+    P = dataclasses.replace(Params(k=24), leaf_capacity=tuned["leaf_capacity"])
+    d.set_tuning(tuned["leaf_ctas_per_sm"])
     mask = torch.empty(total, dtype=torch.uint8, device="cuda")
     score = torch.empty(total, dtype=torch.float32, device="cuda")
     stage = torch.empty(total, dtype=torch.uint8, device="cuda")
@@ -421,8 +429,11 @@ def run_batched(args, stream, flush):
     d.close()
     ps = sorted(plain_ms)
     per_frame_batched = [m / len(frames) for m in batch_ms]
+    default = next((r for r in tuned["table"] if r["leaf_capacity"] == 512 and r["leaf_ctas_per_sm"] == 0), None)
     return {
         "workload": f"{len(frames)} LiDAR frames, {min(sizes)}-{max(sizes)} points, {total} total, K=24",
+        "tuned": {"leaf_capacity": tuned["leaf_capacity"], "leaf_ctas_per_sm": tuned["leaf_ctas_per_sm"],
+                  "batch_ms_at_default_capacity_512": default["ms"] if default else None},
         "batched_points_per_s": total * len(batch_ms) / (sum(batch_ms) / 1000.0),
         "plain_points_per_s": total * len(plain_ms) / len(frames) / (sum(plain_ms) / 1000.0),
         "batched_ms_per_batch": sum(batch_ms) / len(batch_ms),

@@ -126,6 +126,18 @@ int denoise_set_sync(denoise_ctx *ctx, int synchronous);   /* default 1         
 int denoise_set_graphs(denoise_ctx *ctx, int enable);      /* default 0 (direct launches)   */
 int denoise_set_profiling(denoise_ctx *ctx, int enable);   /* per-stage CUDA events, default 0 */
 
+/*
+ * Execution tuning (results do not depend on it).  leaf_ctas_per_sm: how many
+ * persistent CTAs of the fused per-leaf kernel run per SM; 0 (default) = as
+ * many as fit.  The autotuner (paper_2512_10386_gb300/autotune.py) picks it
+ * together with the leaf capacity, which is a method parameter.
+ * Errors: E_INVAL for a NULL context or tuning pointer.
+ */
+typedef struct denoise_tuning {
+  uint32_t leaf_ctas_per_sm;
+} denoise_tuning;
+int denoise_set_tuning(denoise_ctx *ctx, const denoise_tuning *t);
+
 /* Wait for the context's last call on `stream` and return its device-side
  * status (DENOISE_OK, E_NONFINITE or E_TIMEOUT). */
 int denoise_get_status(denoise_ctx *ctx, void *stream);

@@ -31,7 +31,7 @@ EXPORTED = [
     "denoise_create", "denoise_destroy", "denoise_strerror", "denoise_run", "denoise_run_batch",
     "denoise_set_sync", "denoise_set_graphs", "denoise_set_profiling", "denoise_get_status",
     "denoise_get_stats", "denoise_run_debug", "denoise_set_training", "denoise_soft_removal",
-    "denoise_backward", "denoise_run_noalloc",
+    "denoise_backward", "denoise_run_noalloc", "denoise_set_tuning",
 ]
 DENOISE_NOALLOC_MAX_POINTS = 16384
 
@@ -67,6 +67,10 @@ class denoise_stats(ctypes.Structure):
         ("n_stages", ctypes.c_uint32),
         ("stage_ms", ctypes.c_float * 8),
     ]
+
+
+class denoise_tuning(ctypes.Structure):
+    _fields_ = [("leaf_ctas_per_sm", ctypes.c_uint32)]
 
 
 class denoise_debug(ctypes.Structure):
@@ -107,6 +111,7 @@ def lib():
     L.denoise_soft_removal.argtypes = [_V, _V, _V]
     L.denoise_backward.argtypes = [_V, _V, ctypes.POINTER(ctypes.c_double), _V]
     L.denoise_run_noalloc.argtypes = [_V, ctypes.c_size_t, _P, _V, _V, _V, _V]
+    L.denoise_set_tuning.argtypes = [_V, ctypes.POINTER(denoise_tuning)]
     for name in EXPORTED:
         if name != "denoise_strerror":
             getattr(L, name).restype = ctypes.c_int
@@ -172,6 +177,10 @@ def denoise_set_profiling(ctx, on: int) -> int:
 
 def denoise_set_training(ctx, on: int) -> int:
     return lib().denoise_set_training(ctx, int(on))
+
+
+def denoise_set_tuning(ctx, leaf_ctas_per_sm: int = 0) -> int:
+    return lib().denoise_set_tuning(ctx, ctypes.byref(denoise_tuning(leaf_ctas_per_sm)))
 
 
 def denoise_get_status(ctx, stream) -> int:

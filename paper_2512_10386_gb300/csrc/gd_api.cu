@@ -48,6 +48,7 @@ struct denoise_ctx {
   double *h_grad = nullptr;
   // options
   int sync = 1, graphs = 0, profiling = 0, training = 0;
+  uint32_t leaf_ctas_per_sm = 0;
   // last call
   size_t last_n = 0;
   uint32_t last_nframes = 0;
@@ -207,6 +208,7 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
   }
   la.big_scratch = c->d_big;
   la.big_bpp = c->big_bpp;
+  la.ctas_per_sm = c->leaf_ctas_per_sm;
   const int kmax = leaf_kmax(p.k);
   la.lmax = leaf_pick_lmax(p.leaf_capacity, kmax, c->smem_optin - 2048);
   if (c->training) {
@@ -297,6 +299,7 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
     put(&score, sizeof(score));
     put(&stage, sizeof(stage));
     put(&c->training, sizeof(c->training));
+    put(&c->leaf_ctas_per_sm, sizeof(c->leaf_ctas_per_sm));
     put(offsets, sizeof(uint64_t) * (nframes + 1));
     if (!c->gexec || key != c->gkey) {
       if (c->gexec) {
@@ -458,6 +461,12 @@ int denoise_set_graphs(denoise_ctx *ctx, int enable) {
 int denoise_set_profiling(denoise_ctx *ctx, int enable) {
   if (!ctx) return DENOISE_E_INVAL;
   ctx->profiling = enable ? 1 : 0;
+  return DENOISE_OK;
+}
+
+int denoise_set_tuning(denoise_ctx *ctx, const denoise_tuning *t) {
+  if (!ctx || !t) return DENOISE_E_INVAL;
+  ctx->leaf_ctas_per_sm = t->leaf_ctas_per_sm;
   return DENOISE_OK;
 }
 

@@ -146,6 +146,7 @@ struct LeafArgs {
   uint32_t lmax;                // largest leaf handled in shared memory (power of two)
   TrainCache train;
   int use_train;
+  uint32_t ctas_per_sm;         // 0 = occupancy limit
 };
 
 int leaf_kmax(uint32_t k);

@@ -790,6 +790,7 @@ static int launch_k(const LeafArgs &a, int num_sms, cudaStream_t st) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf<KMAX>, kLeafThreads, smem) != cudaSuccess ||
       per_sm < 1)
     return -1;
+  if (a.ctas_per_sm > 0 && (int)a.ctas_per_sm < per_sm) per_sm = (int)a.ctas_per_sm;
   k_leaf<KMAX><<<num_sms * per_sm, kLeafThreads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
