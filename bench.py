@@ -251,15 +251,15 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local).__enter__()   # sampled from warm-up to the end of the GPU sections
-    d.set_profiling(True)
+    # Timed steps are enqueued asynchronously (denoise_set_sync(0)) so that the
+    # events bracket device work only, not the host's wake-up after a sync.
+    d.set_sync(False)
     for _ in range(args.warmup):
         d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    step_ms, leaf_ms = [], []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches = 0
     torch.cuda.synchronize()
     for s in range(args.steps):
         with torch.cuda.stream(stream):
@@ -267,12 +267,22 @@ def run_ours(args):
             ev[s][0].record(stream)
         d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
         ev[s][1].record(stream)
-        st = d.stats()
-        launches += st["launches"]
-        leaf_ms.append(st["stage_ms"][3])
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    from paper_2512_10386_gb300 import _native as N
+    N.check(d.status(stream), "denoise_run")
+    d.set_sync(True)
+    # per-kernel times of the same step (library events between its stages), outside the timed region
+    d.set_profiling(True)
+    leaf_ms = []
+    for s in range(min(args.steps, 10)):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(s))
+        d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
+        leaf_ms.append(d.stats()["stage_ms"][4])
+    d.set_profiling(False)
     stats = d.stats()
+    launches = stats["launches"] * args.steps
     total_ms = max_over_ranks(sum(step_ms), "cuda")
     if dist:
         dist.barrier()
@@ -319,16 +329,18 @@ def run_ours(args):
     # ---- graph-captured replay of the same frame, and the batched workload
     d.set_graphs(True)
     d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
-    g_ms = []
+    d.set_sync(False)
+    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for s in range(args.steps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
             flush.fill_(float(s))
-        a.record(stream)
+        gev[s][0].record(stream)
         d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        g_ms.append(a.elapsed_time(b))
+        gev[s][1].record(stream)
+    torch.cuda.synchronize()
+    N.check(d.status(stream), "denoise_run")
+    d.set_sync(True)
+    g_ms = [a.elapsed_time(b) for a, b in gev]
     d.set_graphs(False)
     graph = {"value": n * args.steps / (sum(g_ms) / 1000.0), "unit": UNIT,
              "ms_per_step": sum(g_ms) / args.steps}
@@ -392,11 +404,13 @@ def run_batched(args, stream, flush):
     d = Denoiser(max_points=total, max_frames=len(frames))
     tuned = tune_batch(xyz, offs, Params(k=24), reps=3, denoiser=d)
     P = dataclasses.replace(Params(k=24), leaf_capacity=tuned["leaf_capacity"])
-    d.set_tuning(tuned["leaf_ctas_per_sm"])
+    d.set_tuning(tuned["leaf_ctas_per_sm"], tuned.get("leaf_smem_points", 0))
     mask = torch.empty(total, dtype=torch.uint8, device="cuda")
     score = torch.empty(total, dtype=torch.float32, device="cuda")
     stage = torch.empty(total, dtype=torch.uint8, device="cuda")
-    # plain path: one call per frame
+    # plain path: one call per frame, enqueued asynchronously like the batch
+    from paper_2512_10386_gb300 import _native as N
+    d.set_sync(False)
     per_frame = []
     for rep in range(args.warmup + max(1, args.steps // 4)):
         for f in range(len(frames)):
@@ -408,14 +422,16 @@ def run_batched(args, stream, flush):
             if rep >= args.warmup:
                 per_frame.append((a, b))
     torch.cuda.synchronize()
+    N.check(d.status(stream), "denoise_run")
     plain_ms = [a.elapsed_time(b) for a, b in per_frame]
     plain_mask = mask.clone()
     # batched path: one graph per batch
     d.set_graphs(True)
     d.run_batch(xyz, offs, P, mask=mask, score=score, stage=stage, stream=stream)
     torch.cuda.synchronize()
+    N.check(d.status(stream), "denoise_run_batch")
     identical = bool(torch.equal(mask, plain_mask))
-    batch_ms = []
+    bev = []
     for s in range(args.warmup + args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
@@ -423,16 +439,21 @@ def run_batched(args, stream, flush):
         a.record(stream)
         d.run_batch(xyz, offs, P, mask=mask, score=score, stage=stage, stream=stream)
         b.record(stream)
-        torch.cuda.synchronize()
         if s >= args.warmup:
-            batch_ms.append(a.elapsed_time(b))
+            bev.append((a, b))
+    torch.cuda.synchronize()
+    N.check(d.status(stream), "denoise_run_batch")
+    batch_ms = [a.elapsed_time(b) for a, b in bev]
+    d.set_sync(True)
     d.close()
     ps = sorted(plain_ms)
     per_frame_batched = [m / len(frames) for m in batch_ms]
-    default = next((r for r in tuned["table"] if r["leaf_capacity"] == 512 and r["leaf_ctas_per_sm"] == 0), None)
+    default = next((r for r in tuned["table"] if r["leaf_capacity"] == 512 and r["leaf_ctas_per_sm"] == 0
+                    and r.get("leaf_smem_points", 0) == 0), None)
     return {
         "workload": f"{len(frames)} LiDAR frames, {min(sizes)}-{max(sizes)} points, {total} total, K=24",
         "tuned": {"leaf_capacity": tuned["leaf_capacity"], "leaf_ctas_per_sm": tuned["leaf_ctas_per_sm"],
+                  "leaf_smem_points": tuned.get("leaf_smem_points", 0),
                   "batch_ms_at_default_capacity_512": default["ms"] if default else None},
         "batched_points_per_s": total * len(batch_ms) / (sum(batch_ms) / 1000.0),
         "plain_points_per_s": total * len(plain_ms) / len(frames) / (sum(plain_ms) / 1000.0),

@@ -127,14 +127,21 @@ int denoise_set_graphs(denoise_ctx *ctx, int enable);      /* default 0 (direct 
 int denoise_set_profiling(denoise_ctx *ctx, int enable);   /* per-stage CUDA events, default 0 */
 
 /*
- * Execution tuning (results do not depend on it).  leaf_ctas_per_sm: how many
- * persistent CTAs of the fused per-leaf kernel run per SM; 0 (default) = as
- * many as fit.  The autotuner (paper_2512_10386_gb300/autotune.py) picks it
- * together with the leaf capacity, which is a method parameter.
+ * Execution tuning (results do not depend on it).
+ *  leaf_ctas_per_sm  how many persistent CTAs of the fused per-leaf kernel run
+ *                    per SM; 0 (default) = as many as fit.
+ *  leaf_smem_points  largest leaf (in points) that the per-leaf kernel keeps in
+ *                    shared memory; larger leaves take its global-memory path.
+ *                    A smaller value shrinks each CTA's shared memory so that
+ *                    more CTAs fit per SM.  Rounded down to a power of two,
+ *                    at least 64; 0 (default) = the leaf capacity.
+ * The autotuner (paper_2512_10386_gb300/autotune.py) picks both together with
+ * the leaf capacity, which is a method parameter.
  * Errors: E_INVAL for a NULL context or tuning pointer.
  */
 typedef struct denoise_tuning {
   uint32_t leaf_ctas_per_sm;
+  uint32_t leaf_smem_points;
 } denoise_tuning;
 int denoise_set_tuning(denoise_ctx *ctx, const denoise_tuning *t);
 
@@ -151,7 +158,7 @@ typedef struct denoise_stats {
   uint64_t n_p2;         /* points that passed the density gate                       */
   uint32_t launches;     /* kernels launched by the call                              */
   uint32_t n_stages;     /* entries valid in stage_ms                                 */
-  float stage_ms[8];     /* with profiling: init+bbox+keys, sort, leaves, leaf kernel, ... */
+  float stage_ms[8];     /* with profiling: init+bbox+keys, sort, leaf finder, leaf prep, fused leaf kernel */
 } denoise_stats;
 
 int denoise_get_stats(denoise_ctx *ctx, denoise_stats *out);
@@ -202,7 +209,7 @@ int denoise_backward(denoise_ctx *ctx, const float *grad_removal, double *grad4,
  * allocation, or inside a real-time loop whose policy forbids cudaMalloc.
  * It denoises one cloud of at most DENOISE_NOALLOC_MAX_POINTS points with
  * exactly the kernels of denoise_run, but all scratch lives in one
- * file-scope device array of the library (6,505,216 bytes per GPU, held by every
+ * file-scope device array of the library (7,291,648 bytes per GPU, held by every
  * GPU that loads the library until the process exits).  Nothing is allocated:
  * no context, no cudaMalloc/cudaFree, no pinned memory.
  *  xyz   [n][3] float32, DEVICE pointer (host pointers are rejected).
@@ -221,6 +228,11 @@ int denoise_backward(denoise_ctx *ctx, const float *grad_removal, double *grad4,
 #define DENOISE_NOALLOC_MAX_POINTS 16384u
 int denoise_run_noalloc(const float *xyz, size_t n, const denoise_params *p, uint8_t *mask, float *score,
                         uint8_t *stage, void *stream);
+/* Size in bytes of denoise_run_noalloc's scratch array (7,291,648); 0 if the
+ * library was built inconsistently (the array would not cover the kernels'
+ * needs, and denoise_run_noalloc then fails with E_INVAL).  Host-only: needs
+ * no GPU. */
+size_t denoise_noalloc_scratch_bytes(void);
 
 #ifdef __cplusplus
 }

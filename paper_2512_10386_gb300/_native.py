@@ -31,7 +31,7 @@ EXPORTED = [
     "denoise_create", "denoise_destroy", "denoise_strerror", "denoise_run", "denoise_run_batch",
     "denoise_set_sync", "denoise_set_graphs", "denoise_set_profiling", "denoise_get_status",
     "denoise_get_stats", "denoise_run_debug", "denoise_set_training", "denoise_soft_removal",
-    "denoise_backward", "denoise_run_noalloc", "denoise_set_tuning",
+    "denoise_backward", "denoise_run_noalloc", "denoise_set_tuning", "denoise_noalloc_scratch_bytes",
 ]
 DENOISE_NOALLOC_MAX_POINTS = 16384
 
@@ -70,7 +70,7 @@ class denoise_stats(ctypes.Structure):
 
 
 class denoise_tuning(ctypes.Structure):
-    _fields_ = [("leaf_ctas_per_sm", ctypes.c_uint32)]
+    _fields_ = [("leaf_ctas_per_sm", ctypes.c_uint32), ("leaf_smem_points", ctypes.c_uint32)]
 
 
 class denoise_debug(ctypes.Structure):
@@ -115,6 +115,8 @@ def lib():
     for name in EXPORTED:
         if name != "denoise_strerror":
             getattr(L, name).restype = ctypes.c_int
+    L.denoise_noalloc_scratch_bytes.argtypes = []
+    L.denoise_noalloc_scratch_bytes.restype = ctypes.c_size_t
     _lib = L
     return L
 
@@ -179,8 +181,8 @@ def denoise_set_training(ctx, on: int) -> int:
     return lib().denoise_set_training(ctx, int(on))
 
 
-def denoise_set_tuning(ctx, leaf_ctas_per_sm: int = 0) -> int:
-    return lib().denoise_set_tuning(ctx, ctypes.byref(denoise_tuning(leaf_ctas_per_sm)))
+def denoise_set_tuning(ctx, leaf_ctas_per_sm: int = 0, leaf_smem_points: int = 0) -> int:
+    return lib().denoise_set_tuning(ctx, ctypes.byref(denoise_tuning(leaf_ctas_per_sm, leaf_smem_points)))
 
 
 def denoise_get_status(ctx, stream) -> int:
@@ -195,6 +197,10 @@ def denoise_get_stats(ctx) -> denoise_stats:
 
 def denoise_soft_removal(ctx, removal_ptr, stream) -> int:
     return lib().denoise_soft_removal(ctx, removal_ptr, stream)
+
+
+def denoise_noalloc_scratch_bytes() -> int:
+    return int(lib().denoise_noalloc_scratch_bytes())
 
 
 def denoise_run_noalloc(xyz_ptr, n, params: denoise_params, mask_ptr, score_ptr, stage_ptr, stream) -> int:

@@ -42,13 +42,21 @@ struct denoise_ctx {
   TrainCache train{};
   bool train_alloc = false;
   // pinned host memory
-  Tile *h_tiles = nullptr;
-  FrameInfo *h_frames = nullptr;
+  // pinned tile/frame tables: a ring of slots, so that a call with a new frame
+  // layout does not wait for the calls still in flight (each slot is rewritten
+  // only after the call that last copied from it has passed `staged`)
+  static constexpr int kSlots = 4;
+  Tile *h_tiles[kSlots] = {};
+  FrameInfo *h_frames[kSlots] = {};
+  cudaEvent_t staged[kSlots] = {};
+  bool staged_rec[kSlots] = {};
+  int slot = 0;
   Counters *h_ctr = nullptr;
   double *h_grad = nullptr;
   // options
   int sync = 1, graphs = 0, profiling = 0, training = 0;
   uint32_t leaf_ctas_per_sm = 0;
+  uint32_t leaf_smem_points = 0;
   // last call
   size_t last_n = 0;
   uint32_t last_nframes = 0;
@@ -58,7 +66,7 @@ struct denoise_ctx {
   int last_status_read = 0;
   float stage_ms[8] = {0};
   int n_stage_ms = 0;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // graph cache (captured on a private stream, launched on the caller's)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -114,9 +122,14 @@ void free_ctx(denoise_ctx *c) {
                    c->train.nbr, c->train.nd2, c->train.ell, c->train.r2, c->train.F, c->train.stage};
   for (void *p : dptrs)
     if (p) cudaFree(p);
-  void *hptrs[] = {c->h_tiles, c->h_frames, c->h_ctr, c->h_grad};
+  void *hptrs[] = {c->h_ctr, c->h_grad};
   for (void *p : hptrs)
     if (p) cudaFreeHost(p);
+  for (int i = 0; i < denoise_ctx::kSlots; ++i) {
+    if (c->h_tiles[i]) cudaFreeHost(c->h_tiles[i]);
+    if (c->h_frames[i]) cudaFreeHost(c->h_frames[i]);
+    if (c->staged[i]) cudaEventDestroy(c->staged[i]);
+  }
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -144,13 +157,14 @@ uint32_t build_tiles(denoise_ctx *c, const uint64_t *offsets, uint32_t nframes) 
   uint32_t nt = 0;
   for (uint32_t f = 0; f < nframes; ++f) {
     const uint32_t b = (uint32_t)offsets[f], e = (uint32_t)offsets[f + 1];
-    c->h_frames[f] = FrameInfo{};
-    c->h_frames[f].begin = b;
-    c->h_frames[f].end = e;
+    FrameInfo &fi = c->h_frames[c->slot][f];
+    fi = FrameInfo{};
+    fi.begin = b;
+    fi.end = e;
     const uint32_t first = nt;
     for (uint32_t s = b; s < e; s += kTilePts) {
       const uint32_t te = (e - s > (uint32_t)kTilePts) ? s + kTilePts : e;
-      c->h_tiles[nt++] = Tile{f, s, te, first};
+      c->h_tiles[c->slot][nt++] = Tile{f, s, te, first};
     }
   }
   return nt;
@@ -166,8 +180,8 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
         cudaSuccess)
       return cuda_fail();
   }
-  cudaMemcpyAsync(c->d_tiles, c->h_tiles, sizeof(Tile) * c->ntiles, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(c->d_frames, c->h_frames, sizeof(FrameInfo) * nframes, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(c->d_tiles, c->h_tiles[c->slot], sizeof(Tile) * c->ntiles, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(c->d_frames, c->h_frames[c->slot], sizeof(FrameInfo) * nframes, cudaMemcpyHostToDevice, st);
   if (use_events) cudaEventRecord(c->ev[0], st);
   FrontArgs fa{};
   fa.xyz = xyz_dev;
@@ -211,14 +225,20 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
   la.ctas_per_sm = c->leaf_ctas_per_sm;
   const int kmax = leaf_kmax(p.k);
   la.lmax = leaf_pick_lmax(p.leaf_capacity, kmax, c->smem_optin - 2048);
+  if (c->leaf_smem_points) {
+    uint32_t l = 64;
+    while (l * 2 <= c->leaf_smem_points) l *= 2;
+    if (l < la.lmax) la.lmax = l;
+  }
   if (c->training) {
     la.train = c->train;
     la.train.k = p.k;
     la.use_train = 1;
   }
-  if (launch_leaf(la, c->num_sms, st)) return cuda_fail();
-  ++launches;
+  if (launch_leaf_prep(la, c->num_sms, st, &launches)) return cuda_fail();
   if (use_events) cudaEventRecord(c->ev[4], st);
+  if (launch_leaf(la, c->num_sms, st, &launches)) return cuda_fail();
+  if (use_events) cudaEventRecord(c->ev[5], st);
   if (mask_h) cudaMemcpyAsync(mask_h, c->d_mask, n, cudaMemcpyDeviceToHost, st);
   if (score_h) cudaMemcpyAsync(score_h, c->d_score, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st);
   if (stage_h) cudaMemcpyAsync(stage_h, c->d_stage, n, cudaMemcpyDeviceToHost, st);
@@ -231,8 +251,8 @@ int finish(denoise_ctx *c, cudaStream_t st, bool events) {
   if (!c->sync) return DENOISE_OK;
   if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_fail();
   if (events) {
-    c->n_stage_ms = 4;
-    for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&c->stage_ms[i], c->ev[i], c->ev[i + 1]);
+    c->n_stage_ms = 5;
+    for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&c->stage_ms[i], c->ev[i], c->ev[i + 1]);
   }
   return map_status(c->h_ctr->status);
 }
@@ -280,7 +300,10 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
   bool layout_changed = c->layout.size() != nframes + 1 ||
                         memcmp(c->layout.data(), offsets, sizeof(uint64_t) * (nframes + 1)) != 0;
   if (layout_changed) {
-    if (c->gexec) cudaStreamSynchronize(st);  // the pinned tables may be read by a graph in flight
+    const int ns = (c->slot + 1) % denoise_ctx::kSlots;
+    if (c->staged_rec[ns] && cudaEventSynchronize(c->staged[ns]) != cudaSuccess)  // slot still being copied
+      return cuda_fail();
+    c->slot = ns;
     c->layout.assign(offsets, offsets + nframes + 1);
     c->ntiles = build_tiles(c, offsets, nframes);
   }
@@ -300,6 +323,7 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
     put(&stage, sizeof(stage));
     put(&c->training, sizeof(c->training));
     put(&c->leaf_ctas_per_sm, sizeof(c->leaf_ctas_per_sm));
+    put(&c->leaf_smem_points, sizeof(c->leaf_smem_points));
     put(offsets, sizeof(uint64_t) * (nframes + 1));
     if (!c->gexec || key != c->gkey) {
       if (c->gexec) {
@@ -333,6 +357,8 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
                  stage_h);
     if (rc) return rc;
   }
+  if (cudaEventRecord(c->staged[c->slot], st) != cudaSuccess) return cuda_fail();
+  c->staged_rec[c->slot] = true;
   c->last_trained = c->training != 0;
   c->last_status_read = 0;
   return finish(c, st, events);
@@ -402,9 +428,11 @@ int denoise_create(denoise_ctx **out, int device, size_t max_points, uint32_t ma
     free_ctx(c);
     return DENOISE_E_NOMEM;
   }
-  if (cudaMallocHost((void **)&c->h_tiles, sizeof(Tile) * c->max_tiles) != cudaSuccess ||
-      cudaMallocHost((void **)&c->h_frames, sizeof(FrameInfo) * max_frames) != cudaSuccess ||
-      cudaMallocHost((void **)&c->h_ctr, sizeof(Counters)) != cudaSuccess ||
+  bool pinned_ok = true;
+  for (int i = 0; i < denoise_ctx::kSlots; ++i)
+    pinned_ok = pinned_ok && cudaMallocHost((void **)&c->h_tiles[i], sizeof(Tile) * c->max_tiles) == cudaSuccess &&
+                cudaMallocHost((void **)&c->h_frames[i], sizeof(FrameInfo) * max_frames) == cudaSuccess;
+  if (!pinned_ok || cudaMallocHost((void **)&c->h_ctr, sizeof(Counters)) != cudaSuccess ||
       cudaMallocHost((void **)&c->h_grad, sizeof(double) * 4) != cudaSuccess) {
     cudaGetLastError();
     free_ctx(c);
@@ -413,6 +441,12 @@ int denoise_create(denoise_ctx **out, int device, size_t max_points, uint32_t ma
   memset(c->h_ctr, 0, sizeof(Counters));
   for (auto &ev : c->ev) {
     if (cudaEventCreate(&ev) != cudaSuccess) {
+      free_ctx(c);
+      return DENOISE_E_CUDA;
+    }
+  }
+  for (auto &ev : c->staged) {
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
       free_ctx(c);
       return DENOISE_E_CUDA;
     }
@@ -467,6 +501,7 @@ int denoise_set_profiling(denoise_ctx *ctx, int enable) {
 int denoise_set_tuning(denoise_ctx *ctx, const denoise_tuning *t) {
   if (!ctx || !t) return DENOISE_E_INVAL;
   ctx->leaf_ctas_per_sm = t->leaf_ctas_per_sm;
+  ctx->leaf_smem_points = t->leaf_smem_points;
   return DENOISE_OK;
 }
 

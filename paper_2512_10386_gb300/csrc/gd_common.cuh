@@ -13,6 +13,8 @@ constexpr float kInvTwo21 = 4.76837158203125e-07f;    // 2^-21
 constexpr int kTilePts = 2048;                        // points per front-end tile
 constexpr int kFrontThreads = 256;
 constexpr int kFrontItems = kTilePts / kFrontThreads; // 8
+static_assert(kFrontThreads == 256, "the radix pass maps one thread to each 8-bit digit");
+static_assert(kTilePts % kFrontThreads == 0, "whole items per thread");
 constexpr int kMaxPasses = 8;                         // 8-bit radix digits over <= 63 key bits
 constexpr uint32_t kSpinLimit = 1u << 22;             // bounded device-side waits
 
@@ -37,9 +39,11 @@ struct Tile {
   uint32_t frame, begin, end, first_tile;  // first_tile: index of the frame's first tile
 };
 
-// Octree leaf.
+// Octree leaf; lo and h (Eq. 10-11) are filled by the leaf-prep kernel.
 struct Leaf {
   uint32_t start, count, frame, level;
+  float lo[3];
+  float h;
 };
 
 struct Counters {
@@ -153,7 +157,10 @@ int leaf_kmax(uint32_t k);
 size_t leaf_smem_bytes(uint32_t lmax, int kmax);
 uint32_t leaf_big_bpp(int kmax);
 uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit);
-int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st);
+// Eq. 10-11 per leaf (box origin lo and voxel size h into the leaf table); must
+// precede launch_leaf on the same stream.
+int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches);
+int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches);
 
 struct BackArgs {
   TrainCache train;

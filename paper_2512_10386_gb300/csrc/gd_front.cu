@@ -368,7 +368,12 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
         e = upper_pre(keys, i, fe, pre, L);
       }
       const uint32_t slot = atomicAdd(&ctr->n_leaves, 1u);
-      leaves[slot] = Leaf{i, e - i, t.frame, (uint32_t)L};
+      Leaf lf{};
+      lf.start = i;
+      lf.count = e - i;
+      lf.frame = t.frame;
+      lf.level = (uint32_t)L;
+      leaves[slot] = lf;
       break;
     }
   }

@@ -26,7 +26,7 @@ constexpr int kLeafThreads = 128;
 constexpr int kLeafWarps = kLeafThreads / 32;
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned long long kInvalid = ~0ull - 1ull;
-constexpr uint32_t kPend = 4;  // parked kNN candidates per lane before a warp-wide merge
+constexpr uint32_t kPend = 8;  // parking slots per lane: a warp merges before any lane could overflow
 // the sort buffer also holds the parked candidates during the kNN
 constexpr size_t kPendBytes = (size_t)kPend * kLeafThreads * sizeof(float);
 
@@ -204,24 +204,9 @@ __device__ __forceinline__ float sqdist(const float4 &a, const float4 &b) {
   return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
-// Sorted register lists (ascending); insert c and drop the largest:
-// L'[s] = min(L[s], max(L[s-1], c)), L'[0] = min(L[0], c).  Every slot uses the
-// old neighbour value, so the KMAX updates are independent (no serial chain).
 // ---------------------------------------------------------------------------
 // per-thread sorted register lists (all indices compile-time)
 // ---------------------------------------------------------------------------
-// insert c, dropping the largest: L'[s] = min(L[s], max(L[s-1], c)), L'[0] =
-// min(L[0], c); every slot reads old values, so the KMAX updates are independent
-template <int KMAX>
-__device__ __forceinline__ void topk_insert(unsigned long long (&L)[KMAX], unsigned long long c) {
-#pragma unroll
-  for (int s = KMAX - 1; s > 0; --s) {
-    const unsigned long long m = L[s - 1] > c ? L[s - 1] : c;
-    L[s] = L[s] < m ? L[s] : m;
-  }
-  L[0] = L[0] < c ? L[0] : c;
-}
-
 // ascending bitonic sort
 template <int N>
 __device__ __forceinline__ void regsort_f(float (&L)[N]) {
@@ -294,52 +279,14 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   const uint32_t lt = lanemask_lt();
   IdxT *nbr = (IdxT *)M.nbr;
 
-  // ---- Eq. 10-11: leaf bounding box, floored extents, adaptive voxel size
-  {
-    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (uint32_t i = tid; i < nt; i += kLeafThreads) {
-      const float4 p = pts[i];
-      mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
-      mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      for (int o = 16; o; o >>= 1) {
-        mn[a] = fminf(mn[a], __shfl_xor_sync(0xFFFFFFFFu, mn[a], o));
-        mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xFFFFFFFFu, mx[a], o));
-      }
-    }
-    if (lane == 0) {
-      for (int a = 0; a < 3; ++a) {
-        S.red[w][a] = __float_as_uint(mn[a]);
-        S.red[w][3 + a] = __float_as_uint(mx[a]);
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      float lo[3], hi[3];
-      for (int a = 0; a < 3; ++a) {
-        lo[a] = __uint_as_float(S.red[0][a]);
-        hi[a] = __uint_as_float(S.red[0][3 + a]);
-        for (int ww = 1; ww < kLeafWarps; ++ww) {
-          lo[a] = fminf(lo[a], __uint_as_float(S.red[ww][a]));
-          hi[a] = fmaxf(hi[a], __uint_as_float(S.red[ww][3 + a]));
-        }
-      }
-      const float delta = A.frames[lf.frame].delta;
-      double H[3];
-      for (int a = 0; a < 3; ++a) {
-        float e = __fsub_rn(hi[a], lo[a]);
-        if (e < delta) e = delta;
-        H[a] = (double)e;
-        S.lo[a] = lo[a];
-      }
-      const double V = __dmul_rn(__dmul_rn(H[0], H[1]), H[2]);
-      const double u = __ddiv_rn(V, (double)nt);
-      S.h = __double2float_rn(__dmul_rn((double)P.beta, cbrt_spec(u)));
-      S.delta = delta;
-      S.run = 0;
-    }
+  // ---- Eq. 10-11: the leaf's box origin and voxel size h come from the prep kernel
+  if (tid == 0) {
+    S.lo[0] = lf.lo[0];
+    S.lo[1] = lf.lo[1];
+    S.lo[2] = lf.lo[2];
+    S.h = lf.h;
+    S.delta = A.frames[lf.frame].delta;
+    S.run = 0;
   }
   // ---- Eq. 12: voxel occupancy (hash with warp-aggregated atomics)
   const uint32_t hcap = pow2ceil(2 * nt);  // <= the carved capacity
@@ -429,14 +376,17 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   // FP32 values (placeholders -1 fill the unused KMAX - k_eff slots).  The list
   // is seeded with the k_eff Morton-order neighbours of the query (window
   // [ws, we]) and sorted once by a register bitonic network.  The scan then
-  // broadcasts every other candidate from shared memory to the warp; a lane
-  // whose candidate beats its current k-th value parks it in its column of a
-  // small shared buffer, and when any lane has kPend parked values the warp
-  // merges them into the lists (sort of kPend values + bitonic merge), so the
-  // list update is paid once per batch rather than once per insertion.
-  // Phase B rescans all candidates: every d^2 < theta is kept and, among the
-  // candidates at exactly theta, those with the smallest input index.  The set
-  // is the k_eff smallest by (d^2, input index), as with a full sort.
+  // broadcasts the other candidates from shared memory to the warp, two per
+  // step (two independent distance chains); a lane whose candidate beats its
+  // current k-th value parks it in its column of a small shared buffer, and
+  // once some lane could overflow its kPend slots at the next step the warp
+  // merges the parked values into the lists (sort of kPend values + bitonic
+  // merge), so the list update is paid once per batch, not per insertion.
+  // Phase B rescans all candidates: every d^2 < theta is kept, the candidates
+  // at exactly theta are counted, and the one with the smallest input index is
+  // kept.  When more than one tie is needed (exact lattices, duplicates) extra
+  // scans take them in input-index order.  The set is the k_eff smallest by
+  // (d^2, input index), as with a full sort.
   {
     // parked candidates live in the sort buffer, idle during the kNN (kPend columns of kLeafThreads)
     float *const pend = reinterpret_cast<float *>(M.sbuf);
@@ -470,13 +420,21 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       uint32_t np = 0;
       for (uint32_t pass = 0; pass < 2; ++pass) {
         const uint32_t jb = pass == 0 ? j0 : 0u, je = pass == 0 ? n1 : j0;
-        for (uint32_t j = jb; j < je; ++j) {
-          const float d2 = sqdist(me, M.p1[j]);
-          if (d2 < L[KMAX - 1] && (j < ws || j > we)) {
-            pend[np * kLeafThreads + tid] = d2;
+        for (uint32_t j = jb; j < je; j += 2) {
+          const bool two = j + 1 < je;
+          const uint32_t j1 = two ? j + 1 : j;
+          const float d0 = sqdist(me, M.p1[j]);
+          const float d1 = sqdist(me, M.p1[j1]);
+          const float thr = L[KMAX - 1];
+          if (d0 < thr && (j < ws || j > we)) {
+            pend[np * kLeafThreads + tid] = d0;
             ++np;
           }
-          if (__any_sync(0xFFFFFFFFu, np == kPend)) {
+          if (two && d1 < thr && (j1 < ws || j1 > we)) {
+            pend[np * kLeafThreads + tid] = d1;
+            ++np;
+          }
+          if (__any_sync(0xFFFFFFFFu, np + 2 > kPend)) {
             merge_pending<KMAX>(L, pend, np, tid);
             np = 0;
           }
@@ -487,49 +445,73 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       uint32_t below = 0;
 #pragma unroll
       for (int sl = 0; sl < KMAX; ++sl) below += (L[sl] >= 0.0f && L[sl] < theta) ? 1u : 0u;
-      const uint32_t ties_needed = keff - below;
-      unsigned long long T[KMAX];  // ties at theta: (input index, position), ascending
-#pragma unroll
-      for (int sl = 0; sl < KMAX; ++sl) T[sl] = kEmpty;
+      const uint32_t ties_needed = keff - below;  // >= 1: theta itself is a candidate
       const uint32_t gq = M.gidx[qq];
-      uint32_t a = 0;
-      for (uint32_t j = 0; j < n1; ++j) {
-        const float4 cj = M.p1[j];
-        const float d2 = sqdist(me, cj);
-        if (j == qq) continue;
-        if (d2 < theta) {
-          if (act && a < keff) {
-            nbr[(size_t)a * cap + qq] = (IdxT)j;
-            if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + a] = __float_as_uint(cj.w);
-            if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + a] = d2;
-            if (A.use_train) {
-              A.train.nbr[(size_t)gq * P.k + a] = __float_as_uint(cj.w);
-              A.train.nd2[(size_t)gq * P.k + a] = d2;
-            }
+      // Record neighbour t of this query (position npos, input index g, distance d2).
+      auto emit = [&](uint32_t t, uint32_t npos, uint32_t g, float d2) {
+        nbr[(size_t)t * cap + qq] = (IdxT)npos;
+        if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = g;
+        if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = d2;
+        if (A.use_train) {
+          A.train.nbr[(size_t)gq * P.k + t] = g;
+          A.train.nd2[(size_t)gq * P.k + t] = d2;
+        }
+      };
+      // every d^2 < theta is a neighbour; among the ntie candidates at exactly
+      // theta the one with the smallest input index is remembered
+      uint32_t a = 0, ntie = 0, tg = 0xFFFFFFFFu, tp = 0;
+      for (uint32_t j = 0; j < n1; j += 2) {
+        const uint32_t j1 = (j + 1 < n1) ? j + 1 : j;
+        const float4 c0 = M.p1[j], c1 = M.p1[j1];
+        const float d0 = sqdist(me, c0), d1 = sqdist(me, c1);
+        if (j != qq) {
+          if (d0 < theta) {
+            if (act && a < keff) emit(a, j, __float_as_uint(c0.w), d0);
+            ++a;
+          } else if (d0 == theta) {
+            ++ntie;
+            if (__float_as_uint(c0.w) < tg) { tg = __float_as_uint(c0.w); tp = j; }
           }
-          ++a;
-        } else if (d2 == theta) {
-          const unsigned long long key = ((unsigned long long)__float_as_uint(cj.w) << 32) | j;
-          if (key < T[KMAX - 1]) topk_insert<KMAX>(T, key);
+        }
+        if (j1 != j && j1 != qq) {
+          if (d1 < theta) {
+            if (act && a < keff) emit(a, j1, __float_as_uint(c1.w), d1);
+            ++a;
+          } else if (d1 == theta) {
+            ++ntie;
+            if (__float_as_uint(c1.w) < tg) { tg = __float_as_uint(c1.w); tp = j1; }
+          }
+        }
+      }
+      if (act && a != below) atomicOr(&A.ctr->status, kStInternal);  // the two phases must agree
+      if (act && below < keff) emit(below, tp, tg, theta);
+      // Several ties needed (rare: exact lattices, duplicate points).  Either all
+      // ties are taken (one more scan), or the ties_needed smallest input indices
+      // are picked one per scan, each the smallest index above the previous one.
+      const uint32_t rounds = (act && ties_needed > 1) ? (ntie == ties_needed ? 1u : ties_needed - 1u) : 0u;
+      const uint32_t max_rounds = __reduce_max_sync(0xFFFFFFFFu, rounds);
+      uint32_t last = tg, slot = below + 1;
+      for (uint32_t r = 0; r < max_rounds; ++r) {
+        const bool all_ties = ntie == ties_needed;
+        uint32_t bg = 0xFFFFFFFFu, bp = 0;
+        for (uint32_t j = 0; j < n1; ++j) {
+          const float4 cj = M.p1[j];
+          const float d2 = sqdist(me, cj);
+          if (r >= rounds || j == qq || d2 != theta) continue;
+          const uint32_t g = __float_as_uint(cj.w);
+          if (all_ties) {
+            if (g != tg && slot < keff) emit(slot++, j, g, theta);
+          } else if (g > last && g < bg) {
+            bg = g;
+            bp = j;
+          }
+        }
+        if (r < rounds && !all_ties && slot < keff) {
+          emit(slot++, bp, bg, theta);
+          last = bg;
         }
       }
       if (act) {
-        if (a != below) atomicOr(&A.ctr->status, kStInternal);  // the two phases must agree
-#pragma unroll
-        for (int sl = 0; sl < KMAX; ++sl) {
-          if ((uint32_t)sl < ties_needed && below + sl < keff && T[sl] != kEmpty) {
-            const uint32_t t = below + sl;
-            const uint32_t npos = (uint32_t)(T[sl] & 0xFFFFFFFFu);
-            const uint32_t g = (uint32_t)(T[sl] >> 32);
-            nbr[(size_t)t * cap + qq] = (IdxT)npos;
-            if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = g;
-            if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = theta;
-            if (A.use_train) {
-              A.train.nbr[(size_t)gq * P.k + t] = g;
-              A.train.nd2[(size_t)gq * P.k + t] = theta;
-            }
-          }
-        }
         for (uint32_t t = keff; t < P.k; ++t) {
           if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
           if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = 0.0f;
@@ -675,6 +657,68 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
 }
 
 // ---------------------------------------------------------------------------
+// leaf prep: Eq. 10-11 for every leaf (all leaves in parallel)
+// ---------------------------------------------------------------------------
+// A block takes 32 leaves at a time: each warp reduces the FP32 bounding boxes
+// of 4 of them (exact min/max), then lane l of warp 0 evaluates leaf l's
+// h = f32(beta * cbrt_spec(V_t / N_t)) with the extents floored at delta and
+// V_t in FP64.  One leaf per lane matters: FP64 issue is scarce on this part,
+// and a warp instruction costs the same with 1 or 32 lanes active.
+constexpr int kPrepThreads = 256;
+constexpr int kPrepLeaves = 32;
+
+__global__ void __launch_bounds__(kPrepThreads) k_leaf_prep(const float4 *__restrict__ spts, Leaf *leaves,
+                                                            const FrameInfo *__restrict__ frames,
+                                                            const Counters *ctr, float beta) {
+  __shared__ float s_ext[kPrepLeaves][3];
+  if (ctr->status & kStFatal) return;
+  const uint32_t nl = ctr->n_leaves;
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr uint32_t kPerWarp = kPrepLeaves / (kPrepThreads / 32);
+  for (uint32_t g = blockIdx.x * kPrepLeaves; g < nl; g += gridDim.x * kPrepLeaves) {
+    for (uint32_t t = 0; t < kPerWarp; ++t) {
+      const uint32_t slot = w * kPerWarp + t, li = g + slot;
+      if (li >= nl) break;
+      const uint32_t start = leaves[li].start, cnt = leaves[li].count;
+      float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (uint32_t i = lane; i < cnt; i += 32) {
+        const float4 p = spts[start + i];
+        mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
+        mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o; o >>= 1) {
+          mn[a] = fminf(mn[a], __shfl_xor_sync(0xFFFFFFFFu, mn[a], o));
+          mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xFFFFFFFFu, mx[a], o));
+        }
+      }
+      if (lane < 3) {
+        const float lo = lane == 0 ? mn[0] : (lane == 1 ? mn[1] : mn[2]);
+        const float hi = lane == 0 ? mx[0] : (lane == 1 ? mx[1] : mx[2]);
+        leaves[li].lo[lane] = lo;
+        s_ext[slot][lane] = __fsub_rn(hi, lo);
+      }
+    }
+    __syncthreads();
+    if (w == 0 && g + lane < nl) {
+      const uint32_t li = g + lane;
+      const float delta = frames[leaves[li].frame].delta;
+      double H[3];
+      for (int a = 0; a < 3; ++a) {
+        float e = s_ext[lane][a];
+        if (e < delta) e = delta;
+        H[a] = (double)e;
+      }
+      const double V = __dmul_rn(__dmul_rn(H[0], H[1]), H[2]);
+      const double u = __ddiv_rn(V, (double)leaves[li].count);
+      leaves[li].h = __double2float_rn(__dmul_rn((double)beta, cbrt_spec(u)));
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // persistent kernel
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
@@ -795,7 +839,14 @@ static int launch_k(const LeafArgs &a, int num_sms, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st) {
+int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches) {
+  k_leaf_prep<<<num_sms * 4, kPrepThreads, 0, st>>>(a.spts, const_cast<Leaf *>(a.leaves), a.frames, a.ctr, a.p.beta);
+  if (launches) ++*launches;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches) {
+  if (launches) ++*launches;
   switch (leaf_kmax(a.p.k)) {
     case 8: return launch_k<8>(a, num_sms, st);
     case 16: return launch_k<16>(a, num_sms, st);

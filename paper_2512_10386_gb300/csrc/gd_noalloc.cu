@@ -23,7 +23,7 @@ namespace {
 constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kN = DENOISE_NOALLOC_MAX_POINTS;
 constexpr size_t kTiles = (kN + kTilePts - 1) / kTilePts;
-constexpr uint32_t kSpillBpp = 336;  // leaf_big_bpp(64): checked against the library at first use
+constexpr uint32_t kSpillBpp = 368;  // leaf_big_bpp(64): checked against the library at first use
 // carve of the scratch array
 constexpr size_t kOffKeys0 = 0;
 constexpr size_t kOffKeys1 = kOffKeys0 + al256(8 * kN);
@@ -98,6 +98,10 @@ __global__ void k_noalloc_tables(FrameInfo *frames, Tile *tiles, uint32_t n) {
   }
 }
 
+extern "C" size_t denoise_noalloc_scratch_bytes(void) {
+  return leaf_big_bpp(64) <= kSpillBpp ? kScratchBytes : 0;
+}
+
 extern "C" int denoise_run_noalloc(const float *xyz, size_t n, const denoise_params *p, uint8_t *mask, float *score,
                                    uint8_t *stage, void *stream) {
   if (!params_ok(p)) return DENOISE_E_INVAL;
@@ -170,7 +174,7 @@ extern "C" int denoise_run_noalloc(const float *xyz, size_t n, const denoise_par
   la.big_scratch = b + kOffSpill;
   la.big_bpp = leaf_big_bpp(64);
   la.lmax = leaf_pick_lmax(p->leaf_capacity, leaf_kmax(p->k), su.smem_optin - 2048);
-  if (launch_leaf(la, su.num_sms, st)) return fail_cuda();
+  if (launch_leaf_prep(la, su.num_sms, st, nullptr) || launch_leaf(la, su.num_sms, st, nullptr)) return fail_cuda();
 
   uint32_t status = 0;
   if (cudaMemcpyAsync(&status, &ctr->status, sizeof(status), cudaMemcpyDeviceToHost, st) != cudaSuccess)

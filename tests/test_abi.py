@@ -24,7 +24,7 @@ def native():
 
 def _declared():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(denoise_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|size_t|const char \*)\s*(denoise_\w+)\s*\(", text, re.M)))
 
 
 def test_header_declares_the_binding_names(native):
@@ -49,15 +49,17 @@ def test_strerror_is_callable_without_gpu(native):
 def test_ctypes_structs_match_c_layout(native, tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gravdenoise.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(denoise_params), sizeof(denoise_stats),'
-                   ' sizeof(denoise_debug), offsetof(denoise_params, temperature), offsetof(denoise_stats, stage_ms));'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(denoise_params), sizeof(denoise_stats),'
+                   ' sizeof(denoise_debug), offsetof(denoise_params, temperature), offsetof(denoise_stats, stage_ms),'
+                   ' sizeof(denoise_tuning), offsetof(denoise_tuning, leaf_smem_points));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(native.denoise_params), ctypes.sizeof(native.denoise_stats),
             ctypes.sizeof(native.denoise_debug), native.denoise_params.temperature.offset,
-            native.denoise_stats.stage_ms.offset]
+            native.denoise_stats.stage_ms.offset, ctypes.sizeof(native.denoise_tuning),
+            native.denoise_tuning.leaf_smem_points.offset]
     assert got == want
 
 
@@ -77,3 +79,15 @@ def test_package_has_no_cpu_fallback(native):
     from paper_2512_10386_gb300 import Denoiser
     with pytest.raises(RuntimeError):
         Denoiser(max_points=10)
+
+
+def test_noalloc_scratch_size_matches_the_header(native):
+    """The no-allocation entry point's static scratch covers the leaf kernel's
+    spill stride (the query returns 0 otherwise) and has the documented size."""
+    import re
+    hdr = open(os.path.join(ROOT, "include", "gravdenoise.h")).read()
+    documented = {int(v.replace(",", "")) for v in re.findall(r"\(([0-9,]+) bytes per GPU", hdr)}
+    documented |= {int(v.replace(",", "")) for v in re.findall(r"scratch array \(([0-9,]+)\)", hdr)}
+    got = native.denoise_noalloc_scratch_bytes()
+    assert got > 0
+    assert documented == {got}

@@ -35,14 +35,16 @@ def test_tuned_batch_equals_per_frame(env, tmp_path):
     xyz = torch.from_numpy(np.concatenate(frames)).cuda()
     P = Params(k=24)
     cache = str(tmp_path / "tune.json")
-    best = tune_batch(xyz, offs, P, capacities=(192, 512), ctas=(0, 2), reps=2, cache_path=cache)
+    best = tune_batch(xyz, offs, P, capacities=(192, 512), ctas=(0, 2), smem_points=(0, 128), reps=2,
+                      cache_path=cache)
     assert best["leaf_capacity"] in (192, 512) and best["leaf_ctas_per_sm"] in (0, 2)
-    assert len(best["table"]) == 4
+    assert best["leaf_smem_points"] in (0, 128)
+    assert len(best["table"]) == 8
     assert tune_batch(xyz, offs, P, cache_path=cache)["leaf_capacity"] == best["leaf_capacity"]  # cached
     import dataclasses
     Pt = dataclasses.replace(P, leaf_capacity=best["leaf_capacity"])
     d = Denoiser(max_points=offs[-1], max_frames=len(frames))
-    d.set_tuning(best["leaf_ctas_per_sm"])
+    d.set_tuning(best["leaf_ctas_per_sm"], best["leaf_smem_points"])
     d.set_graphs(True)
     rb = d.run_batch(xyz, offs, Pt)
     d.set_graphs(False)
@@ -65,3 +67,22 @@ def test_lidar_frame_parity_at_tunable_capacities(env, cap):
     r = env.denoise(xyz, oracle_params(P), debug=True)
     stats = compare_with_oracle(g, r, P)
     print(f"lidar frame cap {cap}:", stats)
+
+
+@pytest.mark.parametrize("smem_points", [64, 256])
+def test_results_do_not_depend_on_the_shared_memory_leaf_size(env, smem_points):
+    """Leaves above leaf_smem_points take the kernel's global-memory path:
+    bit-identical results to the default (every leaf in shared memory)."""
+    import synth
+    from paper_2512_10386_gb300 import Denoiser, Params
+    xyz, _ = synth.superquadric_scan(seed=3, n_surface=120_000)
+    t = torch.from_numpy(xyz).cuda()
+    P = Params(k=32, leaf_capacity=512)
+    d = Denoiser(max_points=len(xyz))
+    ref = d.run(t, P)
+    ref = [x.clone() for x in (ref.mask, ref.score, ref.stage)]
+    d.set_tuning(0, smem_points)
+    got = d.run(t, P)
+    for a, b in zip(ref, (got.mask, got.score, got.stage)):
+        assert torch.equal(a, b)
+    d.close()
