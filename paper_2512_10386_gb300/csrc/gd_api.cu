@@ -33,6 +33,7 @@ struct denoise_ctx {
   uint32_t *d_base = nullptr;
   uint32_t *d_lookback = nullptr;
   Leaf *d_leaves = nullptr;
+  uint32_t *d_order = nullptr;
   Counters *d_ctr = nullptr;
   unsigned char *d_big = nullptr;
   uint32_t big_bpp = 0;
@@ -118,7 +119,7 @@ void free_ctx(denoise_ctx *c) {
   cudaSetDevice(c->device);
   void *dptrs[] = {c->d_xyz, c->d_mask, c->d_score, c->d_stage, c->d_gin, c->d_keys[0], c->d_keys[1],
                    c->d_vals[0], c->d_vals[1], c->d_spts, c->d_frames, c->d_tiles, c->d_hist, c->d_base,
-                   c->d_lookback, c->d_leaves, c->d_ctr, c->d_big, c->d_partials, c->d_grad,
+                   c->d_lookback, c->d_leaves, c->d_order, c->d_ctr, c->d_big, c->d_partials, c->d_grad,
                    c->train.nbr, c->train.nd2, c->train.ell, c->train.r2, c->train.F, c->train.stage};
   for (void *p : dptrs)
     if (p) cudaFree(p);
@@ -210,6 +211,7 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
   la.n = n;
   la.spts = c->d_spts;
   la.leaves = c->d_leaves;
+  la.order = c->d_order;
   la.frames = c->d_frames;
   la.ctr = c->d_ctr;
   la.p = p;
@@ -419,6 +421,7 @@ int denoise_create(denoise_ctx **out, int device, size_t max_points, uint32_t ma
   e |= dalloc(&c->d_base, (size_t)max_frames * kMaxPasses * 256);
   e |= dalloc(&c->d_lookback, (size_t)kMaxPasses * c->max_tiles * 256);
   e |= dalloc(&c->d_leaves, N);
+  e |= dalloc(&c->d_order, N);
   e |= dalloc(&c->d_ctr, 1);
   e |= dalloc(&c->d_big, N * c->big_bpp);
   e |= dalloc(&c->d_partials, kBackPartials * 4);

@@ -46,11 +46,19 @@ struct Leaf {
   float h;
 };
 
+// The fused leaf kernel takes leaves largest first (longest-processing-time
+// order, so that no large leaf starts last and stretches the tail): class 0 =
+// leaves above the shared-memory size (global-memory path), then classes of 64
+// points from the largest down.
+constexpr int kLeafClasses = 9;
+
 struct Counters {
   uint32_t status;
   uint32_t n_leaves;
   uint32_t leaf_work;                    // persistent leaf-kernel work counter
   uint32_t tile_work[kMaxPasses];        // radix-pass tile counters
+  uint32_t cls_count[kLeafClasses];      // leaves per size class
+  uint32_t cls_cursor[kLeafClasses];     // fill cursors of the class-ordered leaf list
   uint32_t pad;
   unsigned long long knn_pairs;
   unsigned long long n_p1;
@@ -137,6 +145,7 @@ struct LeafArgs {
   uint32_t n;                   // total points (bounds check of every output index)
   const float4 *spts;
   const Leaf *leaves;
+  uint32_t *order;              // [n_leaves] leaf indices, largest class first (written by the prep step)
   const FrameInfo *frames;
   Counters *ctr;
   denoise_params p;
@@ -157,8 +166,8 @@ int leaf_kmax(uint32_t k);
 size_t leaf_smem_bytes(uint32_t lmax, int kmax);
 uint32_t leaf_big_bpp(int kmax);
 uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit);
-// Eq. 10-11 per leaf (box origin lo and voxel size h into the leaf table); must
-// precede launch_leaf on the same stream.
+// Eq. 10-11 per leaf (box origin lo and voxel size h into the leaf table) and the
+// largest-first leaf order; must precede launch_leaf on the same stream.
 int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches);
 int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches);
 

@@ -25,6 +25,7 @@ __global__ void k_init(FrameInfo *frames, uint32_t nframes, Counters *ctr, uint3
     ctr->n_leaves = 0;
     ctr->leaf_work = 0;
     for (int i = 0; i < kMaxPasses; ++i) ctr->tile_work[i] = 0;
+    for (int i = 0; i < kLeafClasses; ++i) ctr->cls_count[i] = ctr->cls_cursor[i] = 0;
     ctr->knn_pairs = 0;
     ctr->n_p1 = 0;
     ctr->n_p2 = 0;
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(256) k_digit_scan(const uint32_t *__restrict__
 // one radix pass (stable, segmented by frame, decoupled look-back)
 // ---------------------------------------------------------------------------
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kValMask = (1u << 30) - 1u;
+constexpr int kLookAhead = 4;  // predecessors read per look-back round
 
 template <bool kLast>
 __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
@@ -237,22 +239,33 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
       atomicExch(&lb[d], kFlagInc | run);
     } else {
       atomicExch(&lb[d], kFlagAgg | run);
-      for (int32_t tp = (int32_t)ti - 1; tp >= (int32_t)t.first_tile; --tp) {
-        const uint32_t *q = lookback + (size_t)tp * 256 + d;
-        uint32_t wv = 0;
-        uint32_t it = 0;
-        for (; it < kSpinLimit; ++it) {
-          wv = ld_volatile(q);
-          if (wv & (kFlagAgg | kFlagInc)) break;
-          if (it > 32) __nanosleep(64);
+      // walk back kLookAhead predecessors per round: their flags are read with
+      // independent loads, then consumed in order (a not-yet-published one is
+      // re-read until it is); stop at the first inclusive prefix
+      bool done = false;
+      for (int32_t tp = (int32_t)ti - 1; tp >= (int32_t)t.first_tile && !done; tp -= kLookAhead) {
+        const int32_t cnt = min(kLookAhead, tp - (int32_t)t.first_tile + 1);
+        uint32_t wv[kLookAhead];
+#pragma unroll
+        for (int u = 0; u < kLookAhead; ++u)
+          if (u < cnt) wv[u] = ld_volatile(lookback + (size_t)(tp - u) * 256 + d);
+#pragma unroll
+        for (int u = 0; u < kLookAhead; ++u) {
+          if (u >= cnt || done) break;
+          uint32_t it = 0;
+          for (; it < kSpinLimit && !(wv[u] & (kFlagAgg | kFlagInc)); ++it) {
+            if (it > 32) __nanosleep(64);
+            wv[u] = ld_volatile(lookback + (size_t)(tp - u) * 256 + d);
+          }
+          if (it == kSpinLimit) {
+            atomicOr(&ctr->status, kStTimeout);
+            s_fail = 1;
+            done = true;
+            break;
+          }
+          excl += wv[u] & kValMask;
+          if (wv[u] & kFlagInc) done = true;
         }
-        if (it == kSpinLimit) {
-          atomicOr(&ctr->status, kStTimeout);
-          s_fail = 1;
-          break;
-        }
-        excl += wv & kValMask;
-        if (wv & kFlagInc) break;
       }
       atomicExch(&lb[d], kFlagInc | (excl + run));
     }

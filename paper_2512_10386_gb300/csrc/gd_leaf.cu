@@ -667,9 +667,26 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
 constexpr int kPrepThreads = 256;
 constexpr int kPrepLeaves = 32;
 
+__device__ __forceinline__ uint32_t leaf_class(uint32_t count, uint32_t lmax) {
+  if (count > lmax) return 0;
+  const uint32_t b = (count - 1) >> 6;  // 64-point classes, largest first
+  return 1 + (kLeafClasses - 2) - (b < kLeafClasses - 2 ? b : kLeafClasses - 2);
+}
+
+// warp-aggregated atomicAdd of 1 per lane on ctr[cls]; returns the lane's slot
+__device__ __forceinline__ uint32_t class_slot(uint32_t *ctr, uint32_t cls, uint32_t active) {
+  const uint32_t peers = __match_any_sync(active, cls);
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&ctr[cls], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
 __global__ void __launch_bounds__(kPrepThreads) k_leaf_prep(const float4 *__restrict__ spts, Leaf *leaves,
                                                             const FrameInfo *__restrict__ frames,
-                                                            const Counters *ctr, float beta) {
+                                                            Counters *ctr, float beta, uint32_t lmax) {
   __shared__ float s_ext[kPrepLeaves][3];
   if (ctr->status & kStFatal) return;
   const uint32_t nl = ctr->n_leaves;
@@ -701,8 +718,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_leaf_prep(const float4 *__rest
       }
     }
     __syncthreads();
+    const uint32_t active = __ballot_sync(0xFFFFFFFFu, g + lane < nl);
     if (w == 0 && g + lane < nl) {
       const uint32_t li = g + lane;
+      (void)class_slot(ctr->cls_count, leaf_class(leaves[li].count, lmax), active);
       const float delta = frames[leaves[li].frame].delta;
       double H[3];
       for (int a = 0; a < 3; ++a) {
@@ -715,6 +734,32 @@ __global__ void __launch_bounds__(kPrepThreads) k_leaf_prep(const float4 *__rest
       leaves[li].h = __double2float_rn(__dmul_rn((double)beta, cbrt_spec(u)));
     }
     __syncthreads();
+  }
+}
+
+// Scatter the leaf indices into size-class order (class 0 first); the order
+// within a class is arbitrary and does not affect any result.
+__global__ void __launch_bounds__(256) k_leaf_order(const Leaf *__restrict__ leaves, Counters *ctr,
+                                                    uint32_t *__restrict__ order, uint32_t lmax) {
+  if (ctr->status & kStFatal) return;
+  const uint32_t nl = ctr->n_leaves;
+  __shared__ uint32_t s_base[kLeafClasses];
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int c = 0; c < kLeafClasses; ++c) {
+      s_base[c] = run;
+      run += ctr->cls_count[c];
+    }
+  }
+  __syncthreads();
+  for (uint32_t b = blockIdx.x * blockDim.x; b < nl; b += gridDim.x * blockDim.x) {
+    const uint32_t li = b + threadIdx.x;
+    const uint32_t active = __ballot_sync(0xFFFFFFFFu, li < nl);
+    if (li >= nl) continue;
+    const uint32_t cls = leaf_class(leaves[li].count, lmax);
+    const uint32_t slot = s_base[cls] + class_slot(ctr->cls_cursor, cls, active);
+    if (slot < nl) order[slot] = li;
+    else atomicOr(&ctr->status, kStInternal);
   }
 }
 
@@ -755,9 +800,9 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(const LeafArgs A) {
   for (;;) {
     if (tid == 0) S.leaf = (ld_volatile(&A.ctr->status) & kStFatal) ? 0xFFFFFFFFu : atomicAdd(&A.ctr->leaf_work, 1u);
     __syncthreads();
-    const uint32_t li = S.leaf;  // block-uniform: one thread decided
-    if (li >= n_leaves) break;
-    const Leaf lf = A.leaves[li];
+    const uint32_t wi = S.leaf;  // block-uniform: one thread decided
+    if (wi >= n_leaves) break;
+    const Leaf lf = A.leaves[A.order[wi]];
     if (lf.count <= lmax) {
       if (tid == 0) {
         const uint32_t bytes = lf.count * 16u;
@@ -840,8 +885,10 @@ static int launch_k(const LeafArgs &a, int num_sms, cudaStream_t st) {
 }
 
 int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches) {
-  k_leaf_prep<<<num_sms * 4, kPrepThreads, 0, st>>>(a.spts, const_cast<Leaf *>(a.leaves), a.frames, a.ctr, a.p.beta);
-  if (launches) ++*launches;
+  k_leaf_prep<<<num_sms * 4, kPrepThreads, 0, st>>>(a.spts, const_cast<Leaf *>(a.leaves), a.frames, a.ctr, a.p.beta,
+                                                   a.lmax);
+  k_leaf_order<<<num_sms * 2, 256, 0, st>>>(a.leaves, a.ctr, a.order, a.lmax);
+  if (launches) *launches += 2;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -31,7 +31,8 @@ constexpr size_t kOffVals0 = kOffKeys1 + al256(8 * kN);
 constexpr size_t kOffVals1 = kOffVals0 + al256(4 * kN);
 constexpr size_t kOffSpts = kOffVals1 + al256(4 * kN);
 constexpr size_t kOffLeaves = kOffSpts + al256(16 * kN);
-constexpr size_t kOffFrames = kOffLeaves + al256(sizeof(Leaf) * kN);
+constexpr size_t kOffOrder = kOffLeaves + al256(sizeof(Leaf) * kN);
+constexpr size_t kOffFrames = kOffOrder + al256(4 * kN);
 constexpr size_t kOffTiles = kOffFrames + al256(sizeof(FrameInfo));
 constexpr size_t kOffHist = kOffTiles + al256(sizeof(Tile) * kTiles);
 constexpr size_t kOffBase = kOffHist + al256(4 * kMaxPasses * 256);
@@ -165,6 +166,7 @@ extern "C" int denoise_run_noalloc(const float *xyz, size_t n, const denoise_par
   la.n = nn;
   la.spts = fa.spts;
   la.leaves = fa.leaves;
+  la.order = (uint32_t *)(b + kOffOrder);
   la.frames = frames;
   la.ctr = ctr;
   la.p = *p;
