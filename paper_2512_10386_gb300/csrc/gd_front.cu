@@ -52,13 +52,20 @@ __global__ void __launch_bounds__(kFrontThreads) k_bbox(const float *__restrict_
   const Tile t = tiles[blockIdx.x];
   uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, mx[3] = {0u, 0u, 0u};
   bool bad = false;
-  for (uint32_t i = t.begin + threadIdx.x; i < t.end; i += kFrontThreads) {
-    for (int a = 0; a < 3; ++a) {
-      float v = xyz[3ull * i + a];
-      bad |= !isfinite(v);
-      uint32_t o = f2ord(v);
-      mn[a] = min(mn[a], o);
-      mx[a] = max(mx[a], o);
+  // a tile holds at most kFrontItems points per thread: unrolled, so that all
+  // loads are in flight at once
+#pragma unroll
+  for (int it = 0; it < kFrontItems; ++it) {
+    const uint32_t i = t.begin + it * kFrontThreads + threadIdx.x;
+    if (i < t.end) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float v = xyz[3ull * i + a];
+        bad |= !isfinite(v);
+        const uint32_t o = f2ord(v);
+        mn[a] = min(mn[a], o);
+        mx[a] = max(mx[a], o);
+      }
     }
   }
   for (int a = 0; a < 3; ++a) {
@@ -113,14 +120,18 @@ __global__ void __launch_bounds__(kFrontThreads) k_keys(const float *__restrict_
     f.s = s;
     f.delta = __fmul_rn(side, kInvTwo21);
   }
-  for (uint32_t i = t.begin + threadIdx.x; i < t.end; i += kFrontThreads) {
-    uint32_t q0 = quantise(xyz[3ull * i + 0], lo[0], s);
-    uint32_t q1 = quantise(xyz[3ull * i + 1], lo[1], s);
-    uint32_t q2 = quantise(xyz[3ull * i + 2], lo[2], s);
-    unsigned long long k = morton3(q0, q1, q2);
-    keys[i] = k;
-    vals[i] = i;
-    if (dbg_key) dbg_key[i] = k;
+#pragma unroll
+  for (int it = 0; it < kFrontItems; ++it) {
+    const uint32_t i = t.begin + it * kFrontThreads + threadIdx.x;
+    if (i < t.end) {
+      const uint32_t q0 = quantise(xyz[3ull * i + 0], lo[0], s);
+      const uint32_t q1 = quantise(xyz[3ull * i + 1], lo[1], s);
+      const uint32_t q2 = quantise(xyz[3ull * i + 2], lo[2], s);
+      const unsigned long long k = morton3(q0, q1, q2);
+      keys[i] = k;
+      vals[i] = i;
+      if (dbg_key) dbg_key[i] = k;
+    }
   }
 }
 
@@ -136,9 +147,16 @@ __global__ void __launch_bounds__(kFrontThreads) k_digit_hist(const unsigned lon
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += kFrontThreads) (&sh[0][0])[i] = 0;
   __syncthreads();
   const Tile t = tiles[blockIdx.x];
-  for (uint32_t i = t.begin + threadIdx.x; i < t.end; i += kFrontThreads) {
-    unsigned long long k = keys[i];
-    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k >> (lowbit + 8 * p)) & 0xFFu], 1u);
+  unsigned long long k[kFrontItems];
+#pragma unroll
+  for (int it = 0; it < kFrontItems; ++it) {
+    const uint32_t i = t.begin + it * kFrontThreads + threadIdx.x;
+    k[it] = (i < t.end) ? keys[i] : 0ull;
+  }
+#pragma unroll
+  for (int it = 0; it < kFrontItems; ++it) {
+    if (t.begin + it * kFrontThreads + threadIdx.x < t.end)
+      for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k[it] >> (lowbit + 8 * p)) & 0xFFu], 1u);
   }
   __syncthreads();
   uint32_t *h = hist + (size_t)t.frame * kMaxPasses * 256;
@@ -313,45 +331,66 @@ __device__ __forceinline__ unsigned long long prefix_of(unsigned long long k, in
   return level == 0 ? 0ull : (k >> (63 - 3 * level));
 }
 
-// first index in [lo, hi) whose level-L prefix is >= pre (keys sorted)
-__device__ __forceinline__ uint32_t lower_pre(const unsigned long long *keys, uint32_t lo, uint32_t hi,
-                                              unsigned long long pre, int level) {
+// Binary searches over sorted keys; kb[idx - koff] is the key of sorted
+// position idx (kb = a shared-memory window starting at position koff, or the
+// global array with koff = 0).
+// first index in [lo, hi) whose level-L prefix is >= pre
+__device__ __forceinline__ uint32_t lower_pre(const unsigned long long *kb, uint32_t koff, uint32_t lo,
+                                              uint32_t hi, unsigned long long pre, int level) {
   while (lo < hi) {
     uint32_t mid = lo + ((hi - lo) >> 1);
-    if (prefix_of(keys[mid], level) < pre) lo = mid + 1;
+    if (prefix_of(kb[mid - koff], level) < pre) lo = mid + 1;
     else hi = mid;
   }
   return lo;
 }
 // first index in [lo, hi) whose level-L prefix is > pre
-__device__ __forceinline__ uint32_t upper_pre(const unsigned long long *keys, uint32_t lo, uint32_t hi,
-                                              unsigned long long pre, int level) {
+__device__ __forceinline__ uint32_t upper_pre(const unsigned long long *kb, uint32_t koff, uint32_t lo,
+                                              uint32_t hi, unsigned long long pre, int level) {
   while (lo < hi) {
     uint32_t mid = lo + ((hi - lo) >> 1);
-    if (prefix_of(keys[mid], level) <= pre) lo = mid + 1;
+    if (prefix_of(kb[mid - koff], level) <= pre) lo = mid + 1;
     else hi = mid;
   }
   return lo;
 }
 
+// Largest leaf capacity whose key window fits the leaf finder's static shared-memory budget.
+constexpr uint32_t kLeavesSmemKeys = 6144;  // 48 KB
+constexpr uint32_t kLeavesSmemCap = (kLeavesSmemKeys - kTilePts) / 2 - 1;
+
 // A sorted position i starts a leaf iff it starts its frame, or every octree
 // node shared with position i-1 holds more than leaf_capacity points (so the
 // leaf of i is a proper descendant of the deepest shared node, and begins at i).
+// Every search below stays within cap + 1 positions of i, except the one at the
+// maximum depth D; with cap <= kLeavesSmemCap the block first stages its tile's
+// keys plus that halo on both sides in shared memory and searches there.
 __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long long *__restrict__ keys,
                                                           const Tile *__restrict__ tiles,
                                                           const FrameInfo *__restrict__ frames,
                                                           Leaf *__restrict__ leaves, Counters *ctr,
                                                           uint32_t cap, int D) {
+  extern __shared__ unsigned long long s_win[];
   if (ctr->status & kStFatal) return;
   const Tile t = tiles[blockIdx.x];
   const uint32_t fb = frames[t.frame].begin, fe = frames[t.frame].end;
+  const unsigned long long *kb = keys;
+  uint32_t koff = 0;
+  if (cap <= kLeavesSmemCap) {  // block-uniform
+    const uint32_t wb = (t.begin - fb > cap + 1) ? t.begin - cap - 1 : fb;
+    const uint32_t we = (fe - t.end > cap + 1) ? t.end + cap + 1 : fe;
+    for (uint32_t i = wb + threadIdx.x; i < we; i += kFrontThreads) s_win[i - wb] = keys[i];
+    __syncthreads();
+    kb = s_win;
+    koff = wb;
+  }
   for (uint32_t i = t.begin + threadIdx.x; i < t.end; i += kFrontThreads) {
-    const unsigned long long ki = keys[i];
+    const unsigned long long ki = kb[i - koff];
     int L;  // level of the first node that starts at i
     if (i == fb) {
       L = 0;
     } else {
-      const unsigned long long x = keys[i - 1] ^ ki;
+      const unsigned long long x = kb[i - 1 - koff] ^ ki;
       int l = (x == 0) ? 21 : (__clzll((long long)x) - 1) / 3;  // shared levels below the root
       if (l >= D) continue;                                      // same max-depth node
       // count of the level-l node containing i-1 and i, decided within a window
@@ -362,8 +401,8 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
         const unsigned long long pre = prefix_of(ki, l);
         const uint32_t wlo = (i - fb > cap + 1) ? i - cap - 1 : fb;
         const uint32_t whi = (fe - i > cap + 1) ? i + cap + 1 : fe;
-        const uint32_t a = lower_pre(keys, wlo, i, pre, l);
-        const uint32_t b = upper_pre(keys, i, whi, pre, l);
+        const uint32_t a = lower_pre(kb, koff, wlo, i, pre, l);
+        const uint32_t b = upper_pre(kb, koff, i, whi, pre, l);
         big = (b - a) > cap;
       }
       if (!big) continue;
@@ -375,10 +414,10 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
       uint32_t e;
       if (L < D) {
         const uint32_t whi = (fe - i > cap + 1) ? i + cap + 1 : fe;
-        e = upper_pre(keys, i, whi, pre, L);
+        e = upper_pre(kb, koff, i, whi, pre, L);
         if (e - i > cap) continue;
       } else {
-        e = upper_pre(keys, i, fe, pre, L);
+        e = upper_pre(keys, 0, i, fe, pre, L);  // a max-depth node may be of any size
       }
       const uint32_t slot = atomicAdd(&ctr->n_leaves, 1u);
       Leaf lf{};
@@ -442,8 +481,11 @@ int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t
     ++nl;
   }
   if (ev_after_sort) cudaEventRecord(*ev_after_sort, st);
-  k_leaves<<<a.ntiles, kFrontThreads, 0, st>>>(a.keys[cur], a.tiles, a.frames, a.leaves, a.ctr,
-                                               a.leaf_capacity, a.max_depth);
+  const size_t win = (a.leaf_capacity <= kLeavesSmemCap)
+                        ? sizeof(unsigned long long) * (kTilePts + 2 * ((size_t)a.leaf_capacity + 1))
+                        : 0;
+  k_leaves<<<a.ntiles, kFrontThreads, win, st>>>(a.keys[cur], a.tiles, a.frames, a.leaves, a.ctr,
+                                                 a.leaf_capacity, a.max_depth);
   ++nl;
   if (launches) *launches += nl;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
