@@ -202,8 +202,12 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
     const uint32_t *__restrict__ digit_base, uint32_t *__restrict__ lookback, uint32_t *tile_counter,
     int shift, Counters *ctr) {
   constexpr int W = kFrontThreads / 32;
-  __shared__ uint32_t s_wcnt[W][256];
-  __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_wcnt[W][256];  // per warp and digit: count, then exclusive prefix over warps
+  __shared__ uint32_t s_base[256];     // global output base of each digit for this tile
+  __shared__ uint32_t s_doff[256];     // first position of each digit in the tile's sorted order
+  __shared__ uint32_t s_wsum[W];
+  __shared__ unsigned long long s_key[kTilePts];  // the tile in sorted order, for coalesced writes
+  __shared__ uint32_t s_val[kTilePts];
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_fail;
   if (ctr->status & kStFatal) return;
@@ -219,7 +223,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
   const uint32_t wbase = t.begin + w * 32 * kFrontItems;
 
   unsigned long long key[kFrontItems];
-  uint32_t val[kFrontItems], dig[kFrontItems], rank[kFrontItems];
+  uint32_t val[kFrontItems], dig[kFrontItems], rank[kFrontItems], peers[kFrontItems];
 #pragma unroll
   for (int i = 0; i < kFrontItems; ++i) {
     uint32_t idx = wbase + i * 32 + lane;
@@ -228,20 +232,34 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
     val[i] = ok ? vin[idx] : 0u;
     dig[i] = ok ? (uint32_t)((key[i] >> shift) & 0xFFu) : 256u;
   }
-  const uint32_t lt = lanemask_lt();
+  // lanes of the warp holding the same 9-bit value (8-bit digit or 256 = no item):
+  // one ballot per bit, independent across items
 #pragma unroll
   for (int i = 0; i < kFrontItems; ++i) {
     const uint32_t d = dig[i];
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    uint32_t pm = 0xFFFFFFFFu;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+      const bool bit = (d >> b) & 1u;
+      const uint32_t bb = __ballot_sync(0xFFFFFFFFu, bit);
+      pm &= bit ? bb : ~bb;
+    }
+    peers[i] = pm;
+  }
+  // stable rank within the warp in (item, lane) order = input order
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < kFrontItems; ++i) {
+    const uint32_t d = dig[i], pm = peers[i];
     uint32_t old = 0;
     if (d < 256u) old = s_wcnt[w][d];
     __syncwarp();
-    rank[i] = old + __popc(peers & lt);
-    if (d < 256u && (peers & lt) == 0) s_wcnt[w][d] = old + __popc(peers);
+    rank[i] = old + __popc(pm & lt);
+    if (d < 256u && (pm & lt) == 0) s_wcnt[w][d] = old + __popc(pm);
     __syncwarp();
   }
   __syncthreads();
-  // per digit: exclusive prefix over warps, tile total, then look-back
+  // per digit: exclusive prefix over warps, tile total, position in the tile, then look-back
   {
     const uint32_t d = threadIdx.x;
     uint32_t run = 0;
@@ -251,6 +269,16 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
       s_wcnt[ww][d] = run;
       run += c;
     }
+    uint32_t inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= (uint32_t)o) inc += y;
+    }
+    if (lane == 31) s_wsum[w] = inc;
+    __syncthreads();
+    uint32_t wp = 0;
+    for (uint32_t ww = 0; ww < w; ++ww) wp += s_wsum[ww];
+    s_doff[d] = wp + inc - run;
     uint32_t *lb = lookback + (size_t)ti * 256;
     uint32_t excl = 0;
     if (ti == t.first_tile) {
@@ -291,26 +319,37 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
   }
   __syncthreads();
   if (s_fail) return;
-  const uint32_t fend = frames[t.frame].end, fbeg = frames[t.frame].begin;
+  // the tile in sorted order in shared memory ...
 #pragma unroll
   for (int i = 0; i < kFrontItems; ++i) {
     const uint32_t d = dig[i];
     if (d >= 256u) continue;
-    const uint32_t pos = s_base[d] + s_wcnt[w][d] + rank[i];
+    const uint32_t lp = s_doff[d] + s_wcnt[w][d] + rank[i];  // < tile size by construction
+    s_key[lp] = key[i];
+    s_val[lp] = val[i];
+  }
+  __syncthreads();
+  // ... then written out: consecutive positions of one digit go to consecutive addresses
+  const uint32_t fend = frames[t.frame].end, fbeg = frames[t.frame].begin;
+  const uint32_t cnt = t.end - t.begin;
+  for (uint32_t j = threadIdx.x; j < cnt; j += kFrontThreads) {
+    const unsigned long long k = s_key[j];
+    const uint32_t d = (uint32_t)((k >> shift) & 0xFFu);
+    const uint32_t pos = s_base[d] + (j - s_doff[d]);
     if (pos < fbeg || pos >= fend) {
       atomicOr(&ctr->status, kStInternal);
       continue;
     }
-    kout[pos] = key[i];
+    kout[pos] = k;
+    const uint32_t v = s_val[j];
     if (kLast) {
-      const uint32_t v = val[i];
       if (v >= fend) {  // values are point indices of this batch; never read out of bounds
         atomicOr(&ctr->status, kStInternal);
         continue;
       }
       pout[pos] = make_float4(xyz[3ull * v], xyz[3ull * v + 1], xyz[3ull * v + 2], __uint_as_float(v));
     } else {
-      vout[pos] = val[i];
+      vout[pos] = v;
     }
   }
 }
