@@ -158,14 +158,16 @@ __device__ __forceinline__ uint32_t hash_find(const unsigned long long *hk, uint
   return 0xFFFFFFFFu;
 }
 
-// ascending bitonic sort of n (power of two) keys by the whole block
-__device__ void bitonic_sort(unsigned long long *a, uint32_t n) {
+// Ascending bitonic sort of a[0..n) (n a power of two) by the whole block, one
+// compare-exchange stage per barrier: the general form, for any n.
+template <typename T>
+__device__ void bitonic_sort_smem(T *a, uint32_t n) {
   for (uint32_t k = 2; k <= n; k <<= 1) {
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
       for (uint32_t i = threadIdx.x; i < n; i += kLeafThreads) {
         const uint32_t l = i ^ j;
         if (l > i) {
-          const unsigned long long x = a[i], y = a[l];
+          const T x = a[i], y = a[l];
           const bool asc = (i & k) == 0;
           if ((x > y) == asc) {
             a[i] = y;
@@ -178,23 +180,79 @@ __device__ void bitonic_sort(unsigned long long *a, uint32_t n) {
   }
 }
 
-__device__ void bitonic_sort_u32(uint32_t *a, uint32_t n) {
-  for (uint32_t k = 2; k <= n; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < n; i += kLeafThreads) {
-        const uint32_t l = i ^ j;
-        if (l > i) {
-          const uint32_t x = a[i], y = a[l];
-          const bool asc = (i & k) == 0;
-          if ((x > y) == asc) {
-            a[i] = y;
-            a[l] = x;
+// The same network on N = 128 * E elements held in registers: thread t owns
+// elements t*E .. t*E+E-1 (a padded with `pad` from n up to N).  A stage whose
+// partner distance j is below E stays in the thread, below 32*E it is a warp
+// shuffle, and only the stages with j >= 32*E go through shared memory (3 of
+// the 45 stages at N = 512), so the sort needs a handful of barriers instead of
+// one per stage.  Writes the sorted N elements back to a (a must hold N).
+template <typename T, int E>
+__device__ __forceinline__ void bitonic_sort_regs(T *a, uint32_t n, T pad) {
+  constexpr uint32_t N = (uint32_t)kLeafThreads * E;
+  const uint32_t t = threadIdx.x;
+  T v[E];
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const uint32_t e = t * E + k;
+    v[k] = (e < n) ? a[e] : pad;
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (uint32_t size = 2; size <= N; size <<= 1) {
+#pragma unroll 1
+    for (uint32_t j = size >> 1; j > 0; j >>= 1) {
+      if (j < (uint32_t)E) {  // j is 1 or 2: partners inside the thread
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+          const int l1 = k ^ 1, l2 = k ^ 2;
+          const int l = (j == 1) ? l1 : l2;
+          if ((j == 1 && l1 > k) || (j == 2 && l2 > k && E > 2)) {
+            const bool asc = ((t * E + k) & size) == 0;
+            const T x = v[k], y = (j == 1) ? v[l1 < E ? l1 : k] : v[l2 < E ? l2 : k];
+            const T lo = x < y ? x : y, hi = x < y ? y : x;
+            v[k] = asc ? lo : hi;
+            if (j == 1) v[l1 < E ? l1 : k] = asc ? hi : lo;
+            else v[l2 < E ? l2 : k] = asc ? hi : lo;
+            (void)l;
           }
         }
+      } else if (j < 32u * E) {
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+          const uint32_t e = t * E + k;
+          const T y = __shfl_xor_sync(0xFFFFFFFFu, v[k], j / E);
+          const bool take_min = ((e & j) == 0) == ((e & size) == 0);
+          v[k] = take_min ? (v[k] < y ? v[k] : y) : (v[k] < y ? y : v[k]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < E; ++k) a[t * E + k] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+          const uint32_t e = t * E + k;
+          const T y = a[e ^ j];
+          const bool take_min = ((e & j) == 0) == ((e & size) == 0);
+          v[k] = take_min ? (v[k] < y ? v[k] : y) : (v[k] < y ? y : v[k]);
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
+#pragma unroll
+  for (int k = 0; k < E; ++k) a[t * E + k] = v[k];
+  __syncthreads();
+}
+
+// ascending sort of a[0..n), n a power of two; entries n.. up to the next
+// multiple of 128 (at most 512) may be overwritten with `pad`.  Not inlined:
+// the unrolled networks would otherwise raise the whole kernel's register count.
+template <typename T>
+__device__ __noinline__ void block_sort(T *a, uint32_t n, T pad) {
+  if (n <= kLeafThreads) bitonic_sort_regs<T, 1>(a, n, pad);
+  else if (n <= 2 * kLeafThreads) bitonic_sort_regs<T, 2>(a, n, pad);
+  else if (n <= 4 * kLeafThreads) bitonic_sort_regs<T, 4>(a, n, pad);
+  else bitonic_sort_smem<T>(a, n);
 }
 
 // squared distance with the fixed FP32 operation order of the method's reading:
@@ -533,7 +591,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   uint32_t *const vbuf = reinterpret_cast<uint32_t *>(M.sbuf);
   for (uint32_t i = tid; i < sn; i += kLeafThreads) vbuf[i] = (i < n1) ? __float_as_uint(M.r2[i]) : 0xFFFFFFFFu;
   __syncthreads();
-  bitonic_sort_u32(vbuf, sn);
+  block_sort<uint32_t>(vbuf, sn, 0xFFFFFFFFu);
   if (tid == 0) {
     const double pos = __dadd_rn(__ddiv_rn(__dmul_rn((double)n1, (double)P.rho_percentile), 100.0), 0.5);
     const double cc = ceil(pos);
@@ -633,7 +691,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       M.sbuf[i] = key;
     }
     __syncthreads();
-    bitonic_sort(M.sbuf, sn);
+    block_sort<unsigned long long>(M.sbuf, sn, kEmpty);
     const unsigned long long cut = M.sbuf[S.keep_n - 1];
     for (uint32_t i = tid; i < n1; i += kLeafThreads) {
       if (!M.flag[i]) continue;
@@ -780,7 +838,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(kLeafThreads) k_leaf(const LeafArgs A) {
+// 5 CTAs of 128 threads per SM by registers (at most 102 per thread) for K <= 32;
+// the K = 64 lists need more.
+__global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 5) k_leaf(const LeafArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long s_mbar;
   __shared__ LeafShared S;
