@@ -100,14 +100,19 @@ __device__ __forceinline__ void root_cube(const FrameInfo &f, float lo[3], float
 
 // ---------------------------------------------------------------------------
 // keys: 63-bit Morton key per point, value = global point index; the first
-// tile of each frame publishes the frame's root cube for later kernels.
+// tile of each frame publishes the frame's root cube for later kernels.  The
+// digit histograms of every radix pass (per frame) are accumulated on the way.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kFrontThreads) k_keys(const float *__restrict__ xyz, FrameInfo *frames,
                                                         const Tile *__restrict__ tiles,
                                                         unsigned long long *__restrict__ keys,
                                                         uint32_t *__restrict__ vals, uint64_t *dbg_key,
+                                                        uint32_t *__restrict__ hist, int lowbit, int passes,
                                                         const Counters *ctr) {
+  __shared__ uint32_t sh[kMaxPasses][256];
   if (ctr->status & kStFatal) return;
+  for (int i = threadIdx.x; i < passes * 256; i += kFrontThreads) (&sh[0][0])[i] = 0;
+  __syncthreads();
   const Tile t = tiles[blockIdx.x];
   float lo[3], side, s;
   root_cube(frames[t.frame], lo, side, s);
@@ -131,37 +136,13 @@ __global__ void __launch_bounds__(kFrontThreads) k_keys(const float *__restrict_
       keys[i] = k;
       vals[i] = i;
       if (dbg_key) dbg_key[i] = k;
+      for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k >> (lowbit + 8 * p)) & 0xFFu], 1u);
     }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// upfront digit histograms of every pass, per frame
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kFrontThreads) k_digit_hist(const unsigned long long *__restrict__ keys,
-                                                              const Tile *__restrict__ tiles,
-                                                              uint32_t *__restrict__ hist, int lowbit,
-                                                              int passes, const Counters *ctr) {
-  __shared__ uint32_t sh[kMaxPasses][256];
-  if (ctr->status & kStFatal) return;
-  for (int i = threadIdx.x; i < kMaxPasses * 256; i += kFrontThreads) (&sh[0][0])[i] = 0;
-  __syncthreads();
-  const Tile t = tiles[blockIdx.x];
-  unsigned long long k[kFrontItems];
-#pragma unroll
-  for (int it = 0; it < kFrontItems; ++it) {
-    const uint32_t i = t.begin + it * kFrontThreads + threadIdx.x;
-    k[it] = (i < t.end) ? keys[i] : 0ull;
-  }
-#pragma unroll
-  for (int it = 0; it < kFrontItems; ++it) {
-    if (t.begin + it * kFrontThreads + threadIdx.x < t.end)
-      for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k[it] >> (lowbit + 8 * p)) & 0xFFu], 1u);
   }
   __syncthreads();
   uint32_t *h = hist + (size_t)t.frame * kMaxPasses * 256;
   for (int i = threadIdx.x; i < passes * 256; i += kFrontThreads) {
-    uint32_t v = (&sh[0][0])[i];
+    const uint32_t v = (&sh[0][0])[i];
     if (v) atomicAdd(&h[i], v);
   }
 }
@@ -491,14 +472,14 @@ int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t
     ++nl;
   }
   k_bbox<<<a.ntiles, kFrontThreads, 0, st>>>(a.xyz, a.frames, a.tiles, a.ctr);
-  k_keys<<<a.ntiles, kFrontThreads, 0, st>>>(a.xyz, a.frames, a.tiles, a.keys[0], a.vals[0], a.dbg_key, a.ctr);
+  k_keys<<<a.ntiles, kFrontThreads, 0, st>>>(a.xyz, a.frames, a.tiles, a.keys[0], a.vals[0], a.dbg_key,
+                                             a.digit_hist, lowbit, passes, a.ctr);
   nl += 2;
   if (ev_after_keys) cudaEventRecord(*ev_after_keys, st);
   int cur = 0;
   if (passes > 0) {
-    k_digit_hist<<<a.ntiles, kFrontThreads, 0, st>>>(a.keys[0], a.tiles, a.digit_hist, lowbit, passes, a.ctr);
     k_digit_scan<<<a.nframes * passes, 256, 0, st>>>(a.digit_hist, a.digit_base, a.frames, passes, a.ctr);
-    nl += 2;
+    ++nl;
     for (int p = 0; p < passes; ++p) {
       const int shift = lowbit + 8 * p;
       const uint32_t *base = a.digit_base + p * 256;

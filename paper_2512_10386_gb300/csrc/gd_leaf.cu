@@ -311,6 +311,7 @@ __device__ __forceinline__ void merge_pending(float (&L)[KMAX], const float *pen
   }
 }
 
+template <bool kRec>
 __device__ __forceinline__ void write_point(const LeafArgs &A, uint32_t g, uint8_t mk, float sc, uint8_t st) {
   if (g >= A.n) {  // cannot happen with a consistent sort; never write out of bounds
     atomicOr(&A.ctr->status, kStInternal);
@@ -319,7 +320,7 @@ __device__ __forceinline__ void write_point(const LeafArgs &A, uint32_t g, uint8
   if (A.mask) A.mask[g] = mk;
   if (A.score) A.score[g] = sc;
   if (A.stage) A.stage[g] = st;
-  if (A.use_train) {
+  if (kRec && A.use_train) {
     A.train.stage[g] = st;
     A.train.F[g] = sc;
   }
@@ -328,7 +329,7 @@ __device__ __forceinline__ void write_point(const LeafArgs &A, uint32_t g, uint8
 // ---------------------------------------------------------------------------
 // one leaf
 // ---------------------------------------------------------------------------
-template <int KMAX, typename IdxT>
+template <int KMAX, typename IdxT, bool kRec>
 __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__restrict__ pts, const LeafMem &M,
                              LeafShared &S) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -389,7 +390,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       const uint32_t s = hash_find(M.hkey, hcap, key);
       const uint32_t c = (s == 0xFFFFFFFFu) ? 0u : M.hcnt[s];
       in1 = c >= P.min_vox_count;
-      if (A.use_dbg) {
+      if ((kRec && A.use_dbg)) {
         if (A.dbg.vox_count) A.dbg.vox_count[g] = c;
         if (A.dbg.leaf_start) A.dbg.leaf_start[g] = lf.start - fbeg;
         if (A.dbg.leaf_count) A.dbg.leaf_count[g] = nt;
@@ -397,7 +398,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         if (A.dbg.leaf_rho_med) A.dbg.leaf_rho_med[g] = 0.0;
         if (A.dbg.r2) A.dbg.r2[g] = 0.0f;
       }
-      if (!in1) write_point(A, g, 0, 0.0f, 1);
+      if (!in1) write_point<kRec>(A, g, 0, 0.0f, 1);
     }
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, in1);
     if (lane == 0) S.wsum[w] = __popc(bal);
@@ -419,7 +420,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   }
   const uint32_t n1 = S.run;
   if (n1 <= 1) {  // no neighbour exists: the density gate cannot keep it
-    for (uint32_t i = tid; i < n1; i += kLeafThreads) write_point(A, M.gidx[i], 0, 0.0f, 2);
+    for (uint32_t i = tid; i < n1; i += kLeafThreads) write_point<kRec>(A, M.gidx[i], 0, 0.0f, 2);
     return;
   }
   const uint32_t keff = (P.k < n1 - 1) ? P.k : n1 - 1;
@@ -450,7 +451,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     float *const pend = reinterpret_cast<float *>(M.sbuf);
     const float delta2 = __fmul_rn(S.delta, S.delta);
     const uint32_t cap = M.cap;
-    const bool dbg_n = A.use_dbg && A.dbg.nbr, dbg_d = A.use_dbg && A.dbg.nbr_d2;
+    const bool dbg_n = (kRec && A.use_dbg) && A.dbg.nbr, dbg_d = (kRec && A.use_dbg) && A.dbg.nbr_d2;
     for (uint32_t qb = 0; qb < n1; qb += kLeafThreads) {
       const uint32_t q = qb + tid;
       const bool act = q < n1;
@@ -510,7 +511,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         nbr[(size_t)t * cap + qq] = (IdxT)npos;
         if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = g;
         if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = d2;
-        if (A.use_train) {
+        if ((kRec && A.use_train)) {
           A.train.nbr[(size_t)gq * P.k + t] = g;
           A.train.nd2[(size_t)gq * P.k + t] = d2;
         }
@@ -573,15 +574,15 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         for (uint32_t t = keff; t < P.k; ++t) {
           if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
           if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = 0.0f;
-          if (A.use_train) {
+          if ((kRec && A.use_train)) {
             A.train.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
             A.train.nd2[(size_t)gq * P.k + t] = 0.0f;
           }
         }
         const float rt = (theta < delta2) ? delta2 : theta;
         M.r2[qq] = rt;
-        if (A.use_dbg && A.dbg.r2) A.dbg.r2[gq] = rt;
-        if (A.use_train) A.train.r2[gq] = rt;
+        if ((kRec && A.use_dbg) && A.dbg.r2) A.dbg.r2[gq] = rt;
+        if ((kRec && A.use_train)) A.train.r2[gq] = rt;
       }
     }
   }
@@ -637,7 +638,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     S.keep_n = (uint32_t)ceil((double)P.lambda * (double)m);
     if (S.keep_n > m) S.keep_n = m;
     atomicAdd(&A.ctr->n_p2, (unsigned long long)m);
-    if (A.use_dbg && A.dbg.leaf_rho_med) {  // exact FP64 value for the parity output only
+    if ((kRec && A.use_dbg) && A.dbg.leaf_rho_med) {  // exact FP64 value for the parity output only
       const double k43pi = (4.0 / 3.0) * 3.14159265358979323846;
       auto rho_of = [&](float r2) {
         const double rr = (double)r2;
@@ -656,7 +657,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       const float ell = Lref - 1.5f * log2f(__fdiv_rn(r2, r2ref));  // log2(rho_i / sqrt(rho_med^2 + eps))
       M.wa[i] = half_alpha * ell;
       M.wc[i] = __fdiv_rn(c2, r2);
-      if (A.use_train) A.train.ell[M.gidx[i]] = ell;
+      if ((kRec && A.use_train)) A.train.ell[M.gidx[i]] = ell;
     }
   }
   __syncthreads();
@@ -674,7 +675,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         const float d2 = sqdist(me, M.p1[j]);
         const float wt = exp2f(ai + M.wa[j] - d2 * ci);           // w_den * w_dis (Eq. 17, 19)
         const float D = g2 ? d2 : exp2f(hg * log2f(d2));          // (d^2)^(gamma/2)
-        F += wt / (D + ek);                                       // kernel of Eq. 20
+        F += wt * __frcp_rn(D + ek);                              // kernel of Eq. 20
       }
       M.F[i] = F;
     }
@@ -708,9 +709,9 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   for (uint32_t i = tid; i < n1; i += kLeafThreads) {
     const uint32_t g = M.gidx[i];
     const uint8_t f = M.flag[i];
-    if (f == 0) write_point(A, g, 0, 0.0f, 2);
-    else write_point(A, g, f == 2, M.F[i], f == 2 ? 0 : 3);
-    if (A.use_dbg && A.dbg.leaf_rho_med) A.dbg.leaf_rho_med[g] = rho_med;
+    if (f == 0) write_point<kRec>(A, g, 0, 0.0f, 2);
+    else write_point<kRec>(A, g, f == 2, M.F[i], f == 2 ? 0 : 3);
+    if ((kRec && A.use_dbg) && A.dbg.leaf_rho_med) A.dbg.leaf_rho_med[g] = rho_med;
   }
 }
 
@@ -837,9 +838,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
   return false;
 }
 
-template <int KMAX>
 // 5 CTAs of 128 threads per SM by registers (at most 102 per thread) for K <= 32;
-// the K = 64 lists need more.
+// the K = 64 lists need more.  kRec: the debug / training outputs are written
+// (a separate instantiation, so that the plain path carries none of their code).
+template <int KMAX, bool kRec>
 __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 5) k_leaf(const LeafArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long s_mbar;
@@ -881,11 +883,11 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 5) k_leaf(con
         return;
       }
       phase ^= 1u;
-      process_leaf<KMAX, uint16_t>(A, lf, s_pts, Ms, S);
+      process_leaf<KMAX, uint16_t, kRec>(A, lf, s_pts, Ms, S);
     } else {
       LeafMem Mg;
       carve<uint32_t>(A.big_scratch + (size_t)lf.start * A.big_bpp, lf.count, KMAX, &Mg, 0);
-      process_leaf<KMAX, uint32_t>(A, lf, A.spts + lf.start, Mg, S);
+      process_leaf<KMAX, uint32_t, kRec>(A, lf, A.spts + lf.start, Mg, S);
     }
     __syncthreads();
   }
@@ -924,24 +926,33 @@ uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit) {
   return l;
 }
 
-template <int KMAX>
+template <int KMAX, bool kRec>
 static int launch_k(const LeafArgs &a, int num_sms, cudaStream_t st) {
   const size_t smem = leaf_smem_bytes(a.lmax, KMAX);
-  static size_t configured = 0;
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k_leaf<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return -1;
-    cudaFuncSetAttribute(k_leaf<KMAX>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         (int)cudaSharedmemCarveoutMaxShared);
-    configured = smem;
-  }
+  // per call (function attributes are per device, and calls may come from several threads)
+  if (cudaFuncSetAttribute(k_leaf<KMAX, kRec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return -1;
+  cudaFuncSetAttribute(k_leaf<KMAX, kRec>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf<KMAX>, kLeafThreads, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf<KMAX, kRec>, kLeafThreads, smem) !=
+          cudaSuccess ||
       per_sm < 1)
     return -1;
   if (a.ctas_per_sm > 0 && (int)a.ctas_per_sm < per_sm) per_sm = (int)a.ctas_per_sm;
-  k_leaf<KMAX><<<num_sms * per_sm, kLeafThreads, smem, st>>>(a);
+  k_leaf<KMAX, kRec><<<num_sms * per_sm, kLeafThreads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <bool kRec>
+static int launch_kmax(const LeafArgs &a, int num_sms, cudaStream_t st) {
+  switch (leaf_kmax(a.p.k)) {
+    case 8: return launch_k<8, kRec>(a, num_sms, st);
+    case 16: return launch_k<16, kRec>(a, num_sms, st);
+    case 32: return launch_k<32, kRec>(a, num_sms, st);
+    default: return launch_k<64, kRec>(a, num_sms, st);
+  }
 }
 
 int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches) {
@@ -954,12 +965,7 @@ int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launc
 
 int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches) {
   if (launches) ++*launches;
-  switch (leaf_kmax(a.p.k)) {
-    case 8: return launch_k<8>(a, num_sms, st);
-    case 16: return launch_k<16>(a, num_sms, st);
-    case 32: return launch_k<32>(a, num_sms, st);
-    default: return launch_k<64>(a, num_sms, st);
-  }
+  return (a.use_dbg || a.use_train) ? launch_kmax<true>(a, num_sms, st) : launch_kmax<false>(a, num_sms, st);
 }
 
 }  // namespace gd
