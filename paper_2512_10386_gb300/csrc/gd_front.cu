@@ -75,13 +75,29 @@ __global__ void __launch_bounds__(kFrontThreads) k_bbox(const float *__restrict_
     }
   }
   bad = __any_sync(0xFFFFFFFFu, bad);
-  if ((threadIdx.x & 31) == 0) {
-    FrameInfo &f = frames[t.frame];
+  // block reduction first: one atomic per block and value (all blocks of a
+  // frame update the same six words, so per-warp atomics would serialise)
+  __shared__ uint32_t s_red[kFrontThreads / 32][6];
+  __shared__ int s_bad;
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  if (lane == 0) {
     for (int a = 0; a < 3; ++a) {
-      atomicMin(&f.lo_ord[a], mn[a]);
-      atomicMax(&f.hi_ord[a], mx[a]);
+      s_red[w][a] = mn[a];
+      s_red[w][3 + a] = mx[a];
     }
-    if (bad) atomicOr(&ctr->status, kStNonFinite);
+    if (bad) s_bad = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int v = threadIdx.x;
+    uint32_t r = s_red[0][v];
+    for (int ww = 1; ww < kFrontThreads / 32; ++ww) r = (v < 3) ? min(r, s_red[ww][v]) : max(r, s_red[ww][v]);
+    FrameInfo &f = frames[t.frame];
+    if (v < 3) atomicMin(&f.lo_ord[v], r);
+    else atomicMax(&f.hi_ord[v - 3], r);
+    if (v == 0 && s_bad) atomicOr(&ctr->status, kStNonFinite);
   }
 }
 
@@ -375,9 +391,13 @@ __device__ __forceinline__ uint32_t upper_pre(const unsigned long long *kb, uint
   return lo;
 }
 
-// Largest leaf capacity whose key window fits the leaf finder's static shared-memory budget.
-constexpr uint32_t kLeavesSmemKeys = 6144;  // 48 KB
+// Largest leaf capacity whose key window fits the leaf finder's shared-memory budget
+// (the window and the found-leaf buffer stay within the default 48 KB).
+constexpr uint32_t kLeavesSmemKeys = 4800;  // 37.5 KB of keys
 constexpr uint32_t kLeavesSmemCap = (kLeavesSmemKeys - kTilePts) / 2 - 1;
+// static part: found-leaf buffer (kFrontItems x threads x 5 B) + scan words
+static_assert(kLeavesSmemKeys * 8 + kFrontItems * kFrontThreads * 5 + 64 <= 48 * 1024,
+              "leaf finder shared memory above the default 48 KB");
 
 // A sorted position i starts a leaf iff it starts its frame, or every octree
 // node shared with position i-1 holds more than leaf_capacity points (so the
@@ -404,7 +424,16 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
     kb = s_win;
     koff = wb;
   }
-  for (uint32_t i = t.begin + threadIdx.x; i < t.end; i += kFrontThreads) {
+  // pass 1: each thread finds the leaves that start at its items (count, level)
+  __shared__ uint32_t s_cnt[kFrontItems][kFrontThreads];
+  __shared__ uint8_t s_lvl[kFrontItems][kFrontThreads];
+  __shared__ uint32_t s_wsum[kFrontThreads / 32];
+  __shared__ uint32_t s_base;
+#pragma unroll 1
+  for (int it = 0; it < kFrontItems; ++it) {
+    const uint32_t i = t.begin + it * kFrontThreads + threadIdx.x;
+    s_cnt[it][threadIdx.x] = 0;
+    if (i >= t.end) continue;
     const unsigned long long ki = kb[i - koff];
     int L;  // level of the first node that starts at i
     if (i == fb) {
@@ -439,15 +468,41 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
       } else {
         e = upper_pre(keys, 0, i, fe, pre, L);  // a max-depth node may be of any size
       }
-      const uint32_t slot = atomicAdd(&ctr->n_leaves, 1u);
-      Leaf lf{};
-      lf.start = i;
-      lf.count = e - i;
-      lf.frame = t.frame;
-      lf.level = (uint32_t)L;
-      leaves[slot] = lf;
+      s_cnt[it][threadIdx.x] = e - i;  // >= 1: position i is in its own leaf
+      s_lvl[it][threadIdx.x] = (uint8_t)L;
       break;
     }
+  }
+  // pass 2: one atomic per block reserves the block's leaf slots
+  uint32_t mine = 0;
+#pragma unroll
+  for (int it = 0; it < kFrontItems; ++it) mine += s_cnt[it][threadIdx.x] ? 1u : 0u;
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= (uint32_t)o) inc += y;
+  }
+  if (lane == 31) s_wsum[w] = inc;
+  __syncthreads();
+  uint32_t wp = 0, total = 0;
+  for (int ww = 0; ww < kFrontThreads / 32; ++ww) {
+    if (ww < (int)w) wp += s_wsum[ww];
+    total += s_wsum[ww];
+  }
+  if (threadIdx.x == 0) s_base = total ? atomicAdd(&ctr->n_leaves, total) : 0u;
+  __syncthreads();
+  uint32_t slot = s_base + wp + inc - mine;
+#pragma unroll
+  for (int it = 0; it < kFrontItems; ++it) {
+    const uint32_t c = s_cnt[it][threadIdx.x];
+    if (!c) continue;
+    Leaf lf{};
+    lf.start = t.begin + it * kFrontThreads + threadIdx.x;
+    lf.count = c;
+    lf.frame = t.frame;
+    lf.level = s_lvl[it][threadIdx.x];
+    leaves[slot++] = lf;
   }
 }
 

@@ -516,9 +516,10 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           A.train.nd2[(size_t)gq * P.k + t] = d2;
         }
       };
-      // every d^2 < theta is a neighbour; among the ntie candidates at exactly
-      // theta the one with the smallest input index is remembered
-      uint32_t a = 0, ntie = 0, tg = 0xFFFFFFFFu, tp = 0;
+      // every d^2 < theta is a neighbour; the ntie candidates at exactly theta are
+      // counted and the position of the last one kept (common case: one tie, the
+      // k_eff-th neighbour itself)
+      uint32_t a = 0, ntie = 0, tp = 0;
       for (uint32_t j = 0; j < n1; j += 2) {
         const uint32_t j1 = (j + 1 < n1) ? j + 1 : j;
         const float4 c0 = M.p1[j], c1 = M.p1[j1];
@@ -529,7 +530,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
             ++a;
           } else if (d0 == theta) {
             ++ntie;
-            if (__float_as_uint(c0.w) < tg) { tg = __float_as_uint(c0.w); tp = j; }
+            tp = j;
           }
         }
         if (j1 != j && j1 != qq) {
@@ -538,20 +539,20 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
             ++a;
           } else if (d1 == theta) {
             ++ntie;
-            if (__float_as_uint(c1.w) < tg) { tg = __float_as_uint(c1.w); tp = j1; }
+            tp = j1;
           }
         }
       }
       if (act && a != below) atomicOr(&A.ctr->status, kStInternal);  // the two phases must agree
-      if (act && below < keff) emit(below, tp, tg, theta);
-      // Several ties needed (rare: exact lattices, duplicate points).  Either all
-      // ties are taken (one more scan), or the ties_needed smallest input indices
-      // are picked one per scan, each the smallest index above the previous one.
-      const uint32_t rounds = (act && ties_needed > 1) ? (ntie == ties_needed ? 1u : ties_needed - 1u) : 0u;
+      // ties: with exactly ties_needed of them all are taken, otherwise the
+      // ties_needed smallest input indices (rare: exact lattices, duplicates)
+      const bool all_ties = ntie == ties_needed;
+      if (act && all_ties && ties_needed == 1) emit(below, tp, __float_as_uint(M.p1[tp].w), theta);
+      // one scan emits every tie; or one scan per tie picks the smallest index above the last
+      const uint32_t rounds = !act ? 0u : all_ties ? (ties_needed > 1 ? 1u : 0u) : ties_needed;
       const uint32_t max_rounds = __reduce_max_sync(0xFFFFFFFFu, rounds);
-      uint32_t last = tg, slot = below + 1;
+      uint32_t last = 0, slot = below;
       for (uint32_t r = 0; r < max_rounds; ++r) {
-        const bool all_ties = ntie == ties_needed;
         uint32_t bg = 0xFFFFFFFFu, bp = 0;
         for (uint32_t j = 0; j < n1; ++j) {
           const float4 cj = M.p1[j];
@@ -559,8 +560,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           if (r >= rounds || j == qq || d2 != theta) continue;
           const uint32_t g = __float_as_uint(cj.w);
           if (all_ties) {
-            if (g != tg && slot < keff) emit(slot++, j, g, theta);
-          } else if (g > last && g < bg) {
+            if (slot < keff) emit(slot++, j, g, theta);
+          } else if ((r == 0 || g > last) && g < bg) {
             bg = g;
             bp = j;
           }
@@ -669,15 +670,24 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       if (!M.flag[i]) continue;
       const float4 me = M.p1[i];
       const float ai = M.wa[i], ci = M.wc[i];
-      float F = 0.0f;
-      for (uint32_t t = 0; t < keff; ++t) {
+      // two neighbours per step into two partial sums (independent chains),
+      // F = even-rank terms + odd-rank terms
+      float F0 = 0.0f, F1 = 0.0f;
+      auto term = [&](uint32_t t) {
         const uint32_t j = (uint32_t)nbr[(size_t)t * M.cap + i];
         const float d2 = sqdist(me, M.p1[j]);
         const float wt = exp2f(ai + M.wa[j] - d2 * ci);           // w_den * w_dis (Eq. 17, 19)
         const float D = g2 ? d2 : exp2f(hg * log2f(d2));          // (d^2)^(gamma/2)
-        F += wt * __frcp_rn(D + ek);                              // kernel of Eq. 20
+        return wt * __frcp_rn(D + ek);                            // kernel of Eq. 20
+      };
+      uint32_t t = 0;
+      for (; t + 1 < keff; t += 2) {
+        const float e0 = term(t), e1 = term(t + 1);
+        F0 += e0;
+        F1 += e1;
       }
-      M.F[i] = F;
+      if (t < keff) F0 += term(t);
+      M.F[i] = F0 + F1;
     }
   }
   __syncthreads();

@@ -110,6 +110,18 @@ def test_shallow_octree_large_leaves(dn, orc):
     compare_with_oracle(g, r, P)
 
 
+def test_large_leaf_capacity_global_paths(dn, orc):
+    # capacity 2,000: the leaf finder searches global memory (its shared-memory
+    # key window holds capacities up to 1,375) and leaves above the leaf
+    # kernel's shared-memory size take the global spill area
+    import synth
+    xyz, _ = synth.object_cloud(seed=11, n_surface=12000)
+    P = P_(k=16, leaf_capacity=2000)
+    g, r = run_both(dn, orc, xyz, P)
+    assert r["leaf_count"].max() > 1375
+    compare_with_oracle(g, r, P)
+
+
 def test_max_depth_zero_single_leaf(dn, orc):
     rng = np.random.default_rng(2)
     xyz = rng.normal(size=(700, 3)).astype(np.float32)
