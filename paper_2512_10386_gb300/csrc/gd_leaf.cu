@@ -46,9 +46,23 @@ struct LeafMem {
   float *r2, *wa, *wc, *F;   // [cap] per P_1 position
   uint32_t *gidx;            // [cap] global input index per P_1 position
   uint8_t *flag;             // [cap] 0 removed by density gate, 1 scored, 2 kept
-  void *nbr;                 // [KMAX][cap] neighbour positions (transposed: rank-major)
+  void *nbr;                 // neighbour positions: see nb_bits (shared memory) or [KMAX][cap] u32 (global)
   uint32_t hcap, scap, cap;
 };
+
+// Neighbour table of the shared-memory path: query q owns nb_words(cap, kmax)
+// consecutive 32-bit words holding its neighbour positions as nb_bits(cap)-bit
+// fields, rank t at bit t * nb_bits (a 512-point leaf needs 9 bits, not 16).
+// The packing keeps a 512-point, K = 32 CTA under 45 KB: 5 CTAs per SM.
+__host__ __device__ __forceinline__ uint32_t nb_bits(uint32_t cap) {
+  uint32_t b = 1;
+  while ((1u << b) < cap) ++b;
+  return b;
+}
+// an odd word count per query keeps the lanes of a warp on distinct banks
+__host__ __device__ __forceinline__ uint32_t nb_words(uint32_t cap, int kmax) {
+  return (((uint32_t)kmax * nb_bits(cap) + 31u) / 32u) | 1u;
+}
 
 // Layout of the per-leaf arrays.  `alias_head` bytes at the start (the TMA
 // landing zone of the leaf's raw points) are shared with the hash table and
@@ -60,7 +74,8 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
   // region A: max(raw points + hash table, neighbour table)
   const size_t hash_off = al16(head_bytes);
   const size_t hash_end = hash_off + al16((size_t)hcap * 8) + al16((size_t)hcap * 4);
-  const size_t nbr_bytes = al16((size_t)cap * kmax * sizeof(IdxT));
+  const size_t nbr_bytes = (sizeof(IdxT) == 2) ? al16((size_t)cap * nb_words(cap, kmax) * 4)
+                                               : al16((size_t)cap * kmax * sizeof(IdxT));
   size_t off = hash_end > nbr_bytes ? hash_end : nbr_bytes;
   off = al16(off);
   if (m) {
@@ -337,6 +352,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   const denoise_params &P = A.p;
   const uint32_t lt = lanemask_lt();
   IdxT *nbr = (IdxT *)M.nbr;
+  constexpr bool kPacked = sizeof(IdxT) == 2;  // shared-memory path: bit-packed neighbour table
+  const uint32_t nbB = nb_bits(M.cap), nbW = nb_words(M.cap, KMAX);
 
   // ---- Eq. 10-11: the leaf's box origin and voxel size h come from the prep kernel
   if (tid == 0) {
@@ -507,8 +524,23 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       const uint32_t ties_needed = keff - below;  // >= 1: theta itself is a candidate
       const uint32_t gq = M.gidx[qq];
       // Record neighbour t of this query (position npos, input index g, distance d2).
+      // Ranks come in order t = 0, 1, ...: the packed table is filled through a
+      // bit buffer, one word store per 32 bits.
+      uint32_t *const nbw = reinterpret_cast<uint32_t *>(M.nbr) + (size_t)qq * nbW;
+      unsigned long long nb_acc = 0;
+      uint32_t nb_n = 0, nb_w = 0;
       auto emit = [&](uint32_t t, uint32_t npos, uint32_t g, float d2) {
-        nbr[(size_t)t * cap + qq] = (IdxT)npos;
+        if constexpr (kPacked) {
+          nb_acc |= (unsigned long long)npos << nb_n;
+          nb_n += nbB;
+          if (nb_n >= 32) {
+            nbw[nb_w++] = (uint32_t)nb_acc;
+            nb_acc >>= 32;
+            nb_n -= 32;
+          }
+        } else {
+          nbr[(size_t)t * cap + qq] = (IdxT)npos;
+        }
         if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = g;
         if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = d2;
         if ((kRec && A.use_train)) {
@@ -571,6 +603,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           last = bg;
         }
       }
+      if (kPacked && act && nb_n > 0) nbw[nb_w] = (uint32_t)nb_acc;  // last partial word
       if (act) {
         for (uint32_t t = keff; t < P.k; ++t) {
           if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
@@ -624,18 +657,19 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     if (!(m & 1u)) {
       rb = __uint_as_float(vbuf[m / 2]);
       const float t = __fdiv_rn(ra, rb);
-      lr = 1.0f - log2f(1.0f + t * sqrtf(t));
+      lr = __fsub_rn(1.0f, log2f(__fadd_rn(1.0f, __fmul_rn(t, sqrtf(t)))));
     }
     // log2(rho_med) = log2(rho(ra)) - lr, with log2(rho(ra)) = log2(k_eff) - log2(4/3 pi) - 1.5 log2(ra)
-    const float l_rho_a = log2f((float)keff) - 2.0665336287511624f - 1.5f * log2f(ra);
-    const float l_med = l_rho_a - lr;
+    const float l_rho_a =
+        __fsub_rn(__fsub_rn(log2f((float)keff), 2.0665336287511624f), __fmul_rn(1.5f, log2f(ra)));
+    const float l_med = __fsub_rn(l_rho_a, lr);
     float corr = 0.0f;
     if (P.eps_rho > 0.0f) {
-      const float lx = log2f(P.eps_rho) - 2.0f * l_med;  // log2(eps_rho / rho_med^2)
-      corr = (lx > 100.0f) ? 0.5f * lx : 0.5f * log2f(1.0f + exp2f(lx));
+      const float lx = __fsub_rn(log2f(P.eps_rho), __fmul_rn(2.0f, l_med));  // log2(eps_rho / rho_med^2)
+      corr = (lx > 100.0f) ? __fmul_rn(0.5f, lx) : __fmul_rn(0.5f, log2f(__fadd_rn(1.0f, exp2f(lx))));
     }
     S.r2ref = ra;
-    S.Lref = lr - corr;
+    S.Lref = __fsub_rn(lr, corr);
     S.keep_n = (uint32_t)ceil((double)P.lambda * (double)m);
     if (S.keep_n > m) S.keep_n = m;
     atomicAdd(&A.ctr->n_p2, (unsigned long long)m);
@@ -651,18 +685,21 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   __syncthreads();
   {
     const float r2ref = S.r2ref, Lref = S.Lref;
-    const float half_alpha = 0.5f * P.alpha;
-    const float c2 = 1.4426950408889634f / (2.0f * P.sigma * P.sigma);
+    const float half_alpha = __fmul_rn(0.5f, P.alpha);
+    const float c2 = __fdiv_rn(1.4426950408889634f, __fmul_rn(__fmul_rn(2.0f, P.sigma), P.sigma));
     for (uint32_t i = tid; i < n1; i += kLeafThreads) {
       const float r2 = M.r2[i];
-      const float ell = Lref - 1.5f * log2f(__fdiv_rn(r2, r2ref));  // log2(rho_i / sqrt(rho_med^2 + eps))
-      M.wa[i] = half_alpha * ell;
+      const float ell = __fsub_rn(Lref, __fmul_rn(1.5f, log2f(__fdiv_rn(r2, r2ref))));  // log2(rho_i / sqrt(rho_med^2 + eps))
+      M.wa[i] = __fmul_rn(half_alpha, ell);
       M.wc[i] = __fdiv_rn(c2, r2);
       if ((kRec && A.use_train)) A.train.ell[M.gidx[i]] = ell;
     }
   }
   __syncthreads();
-  // ---- Eq. 15-21: dual-weight gravitational score of every P_2 point
+  // ---- Eq. 15-21: dual-weight gravitational score of every P_2 point.  Every FP32
+  // operation of the score, and of the per-leaf and per-point constants above, is an
+  // explicit round-to-nearest intrinsic: no contraction is left to the compiler, so
+  // the shared-memory and global-memory instantiations give bit-identical scores.
   {
     const bool g2 = (P.gamma == 2.0f);
     const float hg = 0.5f * P.gamma, ek = P.eps_k;
@@ -673,21 +710,36 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       // two neighbours per step into two partial sums (independent chains),
       // F = even-rank terms + odd-rank terms
       float F0 = 0.0f, F1 = 0.0f;
-      auto term = [&](uint32_t t) {
-        const uint32_t j = (uint32_t)nbr[(size_t)t * M.cap + i];
+      const uint32_t *nbr_i = reinterpret_cast<const uint32_t *>(M.nbr) + (size_t)i * nbW;
+      unsigned long long r_acc = 0;
+      uint32_t r_n = 0;
+      const uint32_t r_mask = (1u << nbB) - 1u;
+      auto term = [&](uint32_t t) {  // called for t = 0, 1, ... in order
+        uint32_t j;
+        if constexpr (kPacked) {
+          if (r_n < nbB) {
+            r_acc |= (unsigned long long)(*nbr_i++) << r_n;
+            r_n += 32;
+          }
+          j = (uint32_t)r_acc & r_mask;
+          r_acc >>= nbB;
+          r_n -= nbB;
+        } else {
+          j = (uint32_t)nbr[(size_t)t * M.cap + i];
+        }
         const float d2 = sqdist(me, M.p1[j]);
-        const float wt = exp2f(ai + M.wa[j] - d2 * ci);           // w_den * w_dis (Eq. 17, 19)
-        const float D = g2 ? d2 : exp2f(hg * log2f(d2));          // (d^2)^(gamma/2)
-        return wt * __frcp_rn(D + ek);                            // kernel of Eq. 20
+        const float wt = exp2f(__fmaf_rn(-d2, ci, __fadd_rn(ai, M.wa[j])));  // w_den * w_dis (Eq. 17, 19)
+        const float D = g2 ? d2 : exp2f(__fmul_rn(hg, log2f(d2)));         // (d^2)^(gamma/2)
+        return __fmul_rn(wt, __frcp_rn(__fadd_rn(D, ek)));                // kernel of Eq. 20
       };
       uint32_t t = 0;
       for (; t + 1 < keff; t += 2) {
         const float e0 = term(t), e1 = term(t + 1);
-        F0 += e0;
-        F1 += e1;
+        F0 = __fadd_rn(F0, e0);
+        F1 = __fadd_rn(F1, e1);
       }
-      if (t < keff) F0 += term(t);
-      M.F[i] = F0 + F1;
+      if (t < keff) F0 = __fadd_rn(F0, term(t));
+      M.F[i] = __fadd_rn(F0, F1);
     }
   }
   __syncthreads();
