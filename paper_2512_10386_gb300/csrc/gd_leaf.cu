@@ -452,8 +452,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   // FP32 values (placeholders -1 fill the unused KMAX - k_eff slots).  The list
   // is seeded with the k_eff Morton-order neighbours of the query (window
   // [ws, we]) and sorted once by a register bitonic network.  The scan then
-  // broadcasts the other candidates from shared memory to the warp, two per
-  // step (two independent distance chains); a lane whose candidate beats its
+  // broadcasts the other candidates from shared memory to the warp, four per
+  // step (four independent distance chains); a lane whose candidate beats its
   // current k-th value parks it in its column of a small shared buffer, and
   // once some lane could overflow its kPend slots at the next step the warp
   // merges the parked values into the lists (sort of kPend values + bitonic
@@ -496,21 +496,24 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       uint32_t np = 0;
       for (uint32_t pass = 0; pass < 2; ++pass) {
         const uint32_t jb = pass == 0 ? j0 : 0u, je = pass == 0 ? n1 : j0;
-        for (uint32_t j = jb; j < je; j += 2) {
-          const bool two = j + 1 < je;
-          const uint32_t j1 = two ? j + 1 : j;
-          const float d0 = sqdist(me, M.p1[j]);
-          const float d1 = sqdist(me, M.p1[j1]);
+        for (uint32_t j = jb; j < je; j += 4) {
+          uint32_t jj[4];
+          float dd[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const bool ok = j + u < je;
+            jj[u] = ok ? j + u : j;
+            dd[u] = ok ? sqdist(me, M.p1[jj[u]]) : INFINITY;
+          }
           const float thr = L[KMAX - 1];
-          if (d0 < thr && (j < ws || j > we)) {
-            pend[np * kLeafThreads + tid] = d0;
-            ++np;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (dd[u] < thr && (jj[u] < ws || jj[u] > we)) {
+              pend[np * kLeafThreads + tid] = dd[u];
+              ++np;
+            }
           }
-          if (two && d1 < thr && (j1 < ws || j1 > we)) {
-            pend[np * kLeafThreads + tid] = d1;
-            ++np;
-          }
-          if (__any_sync(0xFFFFFFFFu, np + 2 > kPend)) {
+          if (__any_sync(0xFFFFFFFFu, np + 4 > kPend)) {
             merge_pending<KMAX>(L, pend, np, tid);
             np = 0;
           }
@@ -819,10 +822,20 @@ __global__ void __launch_bounds__(kPrepThreads) k_leaf_prep(const float4 *__rest
       if (li >= nl) break;
       const uint32_t start = leaves[li].start, cnt = leaves[li].count;
       float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-      for (uint32_t i = lane; i < cnt; i += 32) {
-        const float4 p = spts[start + i];
-        mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
-        mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
+      for (uint32_t i0 = lane; i0 < cnt; i0 += 128) {  // four loads in flight per lane
+        float4 p[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t i = i0 + 32u * u;
+          if (i < cnt) p[u] = spts[start + i];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (i0 + 32u * u < cnt) {
+            mn[0] = fminf(mn[0], p[u].x); mn[1] = fminf(mn[1], p[u].y); mn[2] = fminf(mn[2], p[u].z);
+            mx[0] = fmaxf(mx[0], p[u].x); mx[1] = fmaxf(mx[1], p[u].y); mx[2] = fmaxf(mx[2], p[u].z);
+          }
+        }
       }
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
