@@ -458,10 +458,10 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   // once some lane could overflow its kPend slots at the next step the warp
   // merges the parked values into the lists (sort of kPend values + bitonic
   // merge), so the list update is paid once per batch, not per insertion.
-  // Phase B rescans all candidates: every d^2 < theta is kept, the candidates
-  // at exactly theta are counted, and the one with the smallest input index is
-  // kept.  When more than one tie is needed (exact lattices, duplicates) extra
-  // scans take them in input-index order.  The set is the k_eff smallest by
+  // Phase B rescans all candidates (four per step): every d^2 < theta is kept;
+  // the candidates at exactly theta are counted and, when exactly as many ties
+  // as needed exist, all kept.  Otherwise (exact lattices, duplicates) extra
+  // scans take the ties in input-index order.  The set is the k_eff smallest by
   // (d^2, input index), as with a full sort.
   {
     // parked candidates live in the sort buffer, idle during the kNN (kPend columns of kLeafThreads)
@@ -555,26 +555,25 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       // counted and the position of the last one kept (common case: one tie, the
       // k_eff-th neighbour itself)
       uint32_t a = 0, ntie = 0, tp = 0;
-      for (uint32_t j = 0; j < n1; j += 2) {
-        const uint32_t j1 = (j + 1 < n1) ? j + 1 : j;
-        const float4 c0 = M.p1[j], c1 = M.p1[j1];
-        const float d0 = sqdist(me, c0), d1 = sqdist(me, c1);
-        if (j != qq) {
-          if (d0 < theta) {
-            if (act && a < keff) emit(a, j, __float_as_uint(c0.w), d0);
-            ++a;
-          } else if (d0 == theta) {
-            ++ntie;
-            tp = j;
-          }
+      for (uint32_t j = 0; j < n1; j += 4) {
+        float4 cv[4];
+        float dv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          cv[u] = M.p1[(j + u < n1) ? j + u : j];
+          dv[u] = sqdist(me, cv[u]);
         }
-        if (j1 != j && j1 != qq) {
-          if (d1 < theta) {
-            if (act && a < keff) emit(a, j1, __float_as_uint(c1.w), d1);
-            ++a;
-          } else if (d1 == theta) {
-            ++ntie;
-            tp = j1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t ju = j + u;
+          if (ju < n1 && ju != qq) {
+            if (dv[u] < theta) {
+              if (act && a < keff) emit(a, ju, __float_as_uint(cv[u].w), dv[u]);
+              ++a;
+            } else if (dv[u] == theta) {
+              ++ntie;
+              tp = ju;
+            }
           }
         }
       }
