@@ -109,7 +109,7 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
 struct LeafShared {
   uint32_t leaf;
   uint32_t n1, keff, m, keep_n, run;
-  uint32_t Rbits;
+  uint32_t crank;  // Eq. 14 cut rank c, from the top of the ascending r^2 order
   float lo[3], h, delta, r2ref, Lref;
   double rho_med;
   uint32_t wsum[kLeafWarps];
@@ -445,6 +445,11 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     atomicAdd(&A.ctr->knn_pairs, (unsigned long long)n1 * (unsigned long long)(n1 - 1));
     atomicAdd(&A.ctr->n_p1, (unsigned long long)n1);
   }
+  if (tid == kLeafThreads - 1) {  // Eq. 14 rank (FP64, one thread), taken off the later critical path
+    const double pos = __dadd_rn(__ddiv_rn(__dmul_rn((double)n1, (double)P.rho_percentile), 100.0), 0.5);
+    const double cc = ceil(pos);
+    S.crank = (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;
+  }
   const uint32_t sn = pow2ceil(n1);
 
   // ---- kNN on P_1 (excluding self), order by (d^2, input index): one thread per query.
@@ -629,14 +634,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   for (uint32_t i = tid; i < sn; i += kLeafThreads) vbuf[i] = (i < n1) ? __float_as_uint(M.r2[i]) : 0xFFFFFFFFu;
   __syncthreads();
   block_sort<uint32_t>(vbuf, sn, 0xFFFFFFFFu);
-  if (tid == 0) {
-    const double pos = __dadd_rn(__ddiv_rn(__dmul_rn((double)n1, (double)P.rho_percentile), 100.0), 0.5);
-    const double cc = ceil(pos);
-    const uint32_t c = (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;
-    S.Rbits = vbuf[n1 - c];
-  }
-  __syncthreads();
-  const uint32_t Rb = S.Rbits;
+  const uint32_t Rb = vbuf[n1 - S.crank];
   for (uint32_t i = tid; i < n1; i += kLeafThreads) {
     const uint32_t v = vbuf[i];
     if (v <= Rb && (i + 1 == n1 || vbuf[i + 1] > Rb)) S.m = i + 1;
