@@ -404,7 +404,7 @@ def run_batched(args, stream, flush):
     d = Denoiser(max_points=total, max_frames=len(frames))
     tuned = tune_batch(xyz, offs, Params(k=24), reps=3, denoiser=d)
     P = dataclasses.replace(Params(k=24), leaf_capacity=tuned["leaf_capacity"])
-    d.set_tuning(tuned["leaf_ctas_per_sm"], tuned.get("leaf_smem_points", 0))
+    d.set_tuning(tuned["leaf_ctas_per_sm"], tuned.get("leaf_smem_points", 0), tuned.get("leaf_threads", 0))
     mask = torch.empty(total, dtype=torch.uint8, device="cuda")
     score = torch.empty(total, dtype=torch.float32, device="cuda")
     stage = torch.empty(total, dtype=torch.uint8, device="cuda")
@@ -449,11 +449,12 @@ def run_batched(args, stream, flush):
     ps = sorted(plain_ms)
     per_frame_batched = [m / len(frames) for m in batch_ms]
     default = next((r for r in tuned["table"] if r["leaf_capacity"] == 512 and r["leaf_ctas_per_sm"] == 0
-                    and r.get("leaf_smem_points", 0) == 0), None)
+                    and r.get("leaf_smem_points", 0) == 0 and r.get("leaf_threads", 0) == 0), None)
     return {
         "workload": f"{len(frames)} LiDAR frames, {min(sizes)}-{max(sizes)} points, {total} total, K=24",
         "tuned": {"leaf_capacity": tuned["leaf_capacity"], "leaf_ctas_per_sm": tuned["leaf_ctas_per_sm"],
                   "leaf_smem_points": tuned.get("leaf_smem_points", 0),
+                  "leaf_threads": tuned.get("leaf_threads", 0),
                   "batch_ms_at_default_capacity_512": default["ms"] if default else None},
         "batched_points_per_s": total * len(batch_ms) / (sum(batch_ms) / 1000.0),
         "plain_points_per_s": total * len(plain_ms) / len(frames) / (sum(plain_ms) / 1000.0),

@@ -135,13 +135,17 @@ int denoise_set_profiling(denoise_ctx *ctx, int enable);   /* per-stage CUDA eve
  *                    A smaller value shrinks each CTA's shared memory so that
  *                    more CTAs fit per SM.  Rounded down to a power of two,
  *                    at least 64; 0 (default) = the leaf capacity.
+ *  leaf_threads      threads of a per-leaf CTA: 64 or 128 (0 = default 128).
+ *                    64 suits workloads of many small leaves (fewer idle
+ *                    warps per leaf); other values give E_INVAL.
  * The autotuner (paper_2512_10386_gb300/autotune.py) picks both together with
  * the leaf capacity, which is a method parameter.
- * Errors: E_INVAL for a NULL context or tuning pointer.
+ * Errors: E_INVAL for a NULL context or tuning pointer, or leaf_threads not 0, 64 or 128.
  */
 typedef struct denoise_tuning {
   uint32_t leaf_ctas_per_sm;
   uint32_t leaf_smem_points;
+  uint32_t leaf_threads;
 } denoise_tuning;
 int denoise_set_tuning(denoise_ctx *ctx, const denoise_tuning *t);
 

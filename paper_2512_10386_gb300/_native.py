@@ -70,7 +70,8 @@ class denoise_stats(ctypes.Structure):
 
 
 class denoise_tuning(ctypes.Structure):
-    _fields_ = [("leaf_ctas_per_sm", ctypes.c_uint32), ("leaf_smem_points", ctypes.c_uint32)]
+    _fields_ = [("leaf_ctas_per_sm", ctypes.c_uint32), ("leaf_smem_points", ctypes.c_uint32),
+                ("leaf_threads", ctypes.c_uint32)]
 
 
 class denoise_debug(ctypes.Structure):
@@ -181,8 +182,9 @@ def denoise_set_training(ctx, on: int) -> int:
     return lib().denoise_set_training(ctx, int(on))
 
 
-def denoise_set_tuning(ctx, leaf_ctas_per_sm: int = 0, leaf_smem_points: int = 0) -> int:
-    return lib().denoise_set_tuning(ctx, ctypes.byref(denoise_tuning(leaf_ctas_per_sm, leaf_smem_points)))
+def denoise_set_tuning(ctx, leaf_ctas_per_sm: int = 0, leaf_smem_points: int = 0, leaf_threads: int = 0) -> int:
+    return lib().denoise_set_tuning(ctx, ctypes.byref(denoise_tuning(leaf_ctas_per_sm, leaf_smem_points,
+                                                                     leaf_threads)))
 
 
 def denoise_get_status(ctx, stream) -> int:

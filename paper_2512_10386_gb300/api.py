@@ -89,9 +89,10 @@ class Denoiser:
     def set_profiling(self, on: bool):
         N.check(N.denoise_set_profiling(self.ctx, on), "denoise_set_profiling")
 
-    def set_tuning(self, leaf_ctas_per_sm: int = 0, leaf_smem_points: int = 0):
+    def set_tuning(self, leaf_ctas_per_sm: int = 0, leaf_smem_points: int = 0, leaf_threads: int = 0):
         """Execution tuning (``denoise_set_tuning``); results do not depend on it."""
-        N.check(N.denoise_set_tuning(self.ctx, int(leaf_ctas_per_sm), int(leaf_smem_points)), "denoise_set_tuning")
+        N.check(N.denoise_set_tuning(self.ctx, int(leaf_ctas_per_sm), int(leaf_smem_points), int(leaf_threads)),
+                "denoise_set_tuning")
 
     def set_training(self, on: bool):
         N.check(N.denoise_set_training(self.ctx, on), "denoise_set_training")

@@ -10,6 +10,9 @@ It measures a workload under candidate settings and keeps the fastest:
   * leaf_smem_points -- largest leaf kept in shared memory; larger leaves take
     the kernel's global-memory path, and each CTA needs less shared memory, so
     more CTAs fit per SM (execution only).
+  * leaf_threads -- 128 (0) or 64 threads per leaf CTA; 64 leaves fewer warps
+    idle on small leaves (execution only).  With 64 the CTA count per SM is
+    left at the occupancy limit.
 The kNN tile is the whole leaf (it is staged in shared memory at once), so
 there is no separate k-tile to tune; the block shape is fixed at compile time.
 Results are cached as JSON keyed by (GPU name, K, frame count, size bucket).
@@ -18,6 +21,7 @@ Results are cached as JSON keyed by (GPU name, K, frame count, size bucket).
 from __future__ import annotations
 
 import dataclasses
+import itertools
 import json
 import math
 import os
@@ -31,6 +35,7 @@ from .api import Denoiser, Params
 DEFAULT_CAPACITIES = (128, 192, 256, 384, 512)
 DEFAULT_CTAS = (0, 2, 3)
 DEFAULT_SMEM_POINTS = (0, 128, 256)
+DEFAULT_THREADS = (0, 64)
 
 
 def _cache_key(params: Params, offsets: Sequence[int]) -> str:
@@ -38,14 +43,15 @@ def _cache_key(params: Params, offsets: Sequence[int]) -> str:
     n = int(offsets[-1])
     frames = len(offsets) - 1
     bucket = 2 ** int(math.ceil(math.log2(max(n, 1))))
-    return f"{name}|k={params.k}|frames={frames}|points<={bucket}|v2"
+    return f"{name}|k={params.k}|frames={frames}|points<={bucket}|v3"
 
 
 def tune_batch(xyz: torch.Tensor, offsets: Sequence[int], params: Params,
                capacities: Iterable[int] = DEFAULT_CAPACITIES, ctas: Iterable[int] = DEFAULT_CTAS,
-               smem_points: Iterable[int] = DEFAULT_SMEM_POINTS, reps: int = 5, cache_path: Optional[str] = None, denoiser: Optional[Denoiser] = None) -> dict:
+               smem_points: Iterable[int] = DEFAULT_SMEM_POINTS, threads: Iterable[int] = DEFAULT_THREADS,
+               reps: int = 5, cache_path: Optional[str] = None, denoiser: Optional[Denoiser] = None) -> dict:
     """Time ``denoise_run_batch`` (graph mode) for every candidate; return the best
-    ``{"leaf_capacity", "leaf_ctas_per_sm", "leaf_smem_points", "ms", "table"}``
+    ``{"leaf_capacity", "leaf_ctas_per_sm", "leaf_smem_points", "leaf_threads", "ms", "table"}``
     (from the cache if present)."""
     key = _cache_key(params, offsets)
     if cache_path and os.path.exists(cache_path):
@@ -65,28 +71,26 @@ def tune_batch(xyz: torch.Tensor, offsets: Sequence[int], params: Params,
     try:
         d.set_graphs(True)
         d.set_sync(False)   # enqueue back to back: the events then bracket device work only
-        for cap in capacities:
+        for cap, nt, c, sp in itertools.product(capacities, threads, ctas, smem_points):
+            if (nt and c) or (sp and sp >= cap):
+                continue  # 64-thread CTAs run at the occupancy limit; sp >= cap is the same as 0
             p = dataclasses.replace(params, leaf_capacity=int(cap))
-            for c in ctas:
-                for sp in smem_points:
-                    if sp and sp >= cap:
-                        continue   # same as 0 (the whole leaf capacity in shared memory)
-                    d.set_tuning(int(c), int(sp))
-                    d.run_batch(xyz, offsets, p, mask=mask, score=score, stage=stage, stream=stream)  # capture
-                    d.run_batch(xyz, offsets, p, mask=mask, score=score, stage=stage, stream=stream)
-                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-                    ev[0].record(stream)
-                    for _ in range(reps):
-                        d.run_batch(xyz, offsets, p, mask=mask, score=score, stage=stage, stream=stream)
-                    ev[1].record(stream)
-                    torch.cuda.synchronize()
-                    N.check(d.status(stream), "denoise_run_batch")
-                    table.append({"leaf_capacity": int(cap), "leaf_ctas_per_sm": int(c),
-                                  "leaf_smem_points": int(sp), "ms": ev[0].elapsed_time(ev[1]) / reps})
+            d.set_tuning(int(c), int(sp), int(nt))
+            d.run_batch(xyz, offsets, p, mask=mask, score=score, stage=stage, stream=stream)  # capture
+            d.run_batch(xyz, offsets, p, mask=mask, score=score, stage=stage, stream=stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            for _ in range(reps):
+                d.run_batch(xyz, offsets, p, mask=mask, score=score, stage=stage, stream=stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            N.check(d.status(stream), "denoise_run_batch")
+            table.append({"leaf_capacity": int(cap), "leaf_ctas_per_sm": int(c), "leaf_smem_points": int(sp),
+                          "leaf_threads": int(nt), "ms": ev[0].elapsed_time(ev[1]) / reps})
     finally:
         d.set_sync(True)
         d.set_graphs(False)
-        d.set_tuning(0, 0)
+        d.set_tuning(0, 0, 0)
         if own:
             d.close()
     best = min(table, key=lambda r: r["ms"])

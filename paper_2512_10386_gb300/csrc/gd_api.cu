@@ -58,6 +58,7 @@ struct denoise_ctx {
   int sync = 1, graphs = 0, profiling = 0, training = 0;
   uint32_t leaf_ctas_per_sm = 0;
   uint32_t leaf_smem_points = 0;
+  uint32_t leaf_threads = 0;
   // last call
   size_t last_n = 0;
   uint32_t last_nframes = 0;
@@ -225,6 +226,7 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
   la.big_scratch = c->d_big;
   la.big_bpp = c->big_bpp;
   la.ctas_per_sm = c->leaf_ctas_per_sm;
+  la.threads = c->leaf_threads;
   const int kmax = leaf_kmax(p.k);
   la.lmax = leaf_pick_lmax(p.leaf_capacity, kmax, c->smem_optin - 2048);
   if (c->leaf_smem_points) {
@@ -326,6 +328,7 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
     put(&c->training, sizeof(c->training));
     put(&c->leaf_ctas_per_sm, sizeof(c->leaf_ctas_per_sm));
     put(&c->leaf_smem_points, sizeof(c->leaf_smem_points));
+    put(&c->leaf_threads, sizeof(c->leaf_threads));
     put(offsets, sizeof(uint64_t) * (nframes + 1));
     if (!c->gexec || key != c->gkey) {
       if (c->gexec) {
@@ -503,8 +506,10 @@ int denoise_set_profiling(denoise_ctx *ctx, int enable) {
 
 int denoise_set_tuning(denoise_ctx *ctx, const denoise_tuning *t) {
   if (!ctx || !t) return DENOISE_E_INVAL;
+  if (t->leaf_threads != 0 && t->leaf_threads != 64 && t->leaf_threads != 128) return DENOISE_E_INVAL;
   ctx->leaf_ctas_per_sm = t->leaf_ctas_per_sm;
   ctx->leaf_smem_points = t->leaf_smem_points;
+  ctx->leaf_threads = t->leaf_threads;
   return DENOISE_OK;
 }
 

@@ -160,6 +160,7 @@ struct LeafArgs {
   TrainCache train;
   int use_train;
   uint32_t ctas_per_sm;         // 0 = occupancy limit
+  uint32_t threads;             // threads per leaf CTA: 64 or 128 (0 = 128)
 };
 
 int leaf_kmax(uint32_t k);

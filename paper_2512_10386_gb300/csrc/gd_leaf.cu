@@ -179,7 +179,7 @@ template <typename T>
 __device__ void bitonic_sort_smem(T *a, uint32_t n) {
   for (uint32_t k = 2; k <= n; k <<= 1) {
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < n; i += kLeafThreads) {
+      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
         const uint32_t l = i ^ j;
         if (l > i) {
           const T x = a[i], y = a[l];
@@ -195,15 +195,16 @@ __device__ void bitonic_sort_smem(T *a, uint32_t n) {
   }
 }
 
-// The same network on N = 128 * E elements held in registers: thread t owns
+// The same network on N = blockDim.x * E elements held in registers: thread t owns
 // elements t*E .. t*E+E-1 (a padded with `pad` from n up to N).  A stage whose
 // partner distance j is below E stays in the thread, below 32*E it is a warp
 // shuffle, and only the stages with j >= 32*E go through shared memory (3 of
-// the 45 stages at N = 512), so the sort needs a handful of barriers instead of
-// one per stage.  Writes the sorted N elements back to a (a must hold N).
+// the 45 stages at N = 512 with 128 threads), so the sort needs a handful of
+// barriers instead of one per stage.  Writes the sorted N elements back to a
+// (a must hold N).
 template <typename T, int E>
 __device__ __forceinline__ void bitonic_sort_regs(T *a, uint32_t n, T pad) {
-  constexpr uint32_t N = (uint32_t)kLeafThreads * E;
+  const uint32_t N = blockDim.x * E;
   const uint32_t t = threadIdx.x;
   T v[E];
 #pragma unroll
@@ -216,19 +217,20 @@ __device__ __forceinline__ void bitonic_sort_regs(T *a, uint32_t n, T pad) {
   for (uint32_t size = 2; size <= N; size <<= 1) {
 #pragma unroll 1
     for (uint32_t j = size >> 1; j > 0; j >>= 1) {
-      if (j < (uint32_t)E) {  // j is 1 or 2: partners inside the thread
+      if (j < (uint32_t)E) {  // partners inside the thread (register indices fixed per jj)
 #pragma unroll
-        for (int k = 0; k < E; ++k) {
-          const int l1 = k ^ 1, l2 = k ^ 2;
-          const int l = (j == 1) ? l1 : l2;
-          if ((j == 1 && l1 > k) || (j == 2 && l2 > k && E > 2)) {
-            const bool asc = ((t * E + k) & size) == 0;
-            const T x = v[k], y = (j == 1) ? v[l1 < E ? l1 : k] : v[l2 < E ? l2 : k];
-            const T lo = x < y ? x : y, hi = x < y ? y : x;
-            v[k] = asc ? lo : hi;
-            if (j == 1) v[l1 < E ? l1 : k] = asc ? hi : lo;
-            else v[l2 < E ? l2 : k] = asc ? hi : lo;
-            (void)l;
+        for (int jj = 1; jj < E; jj <<= 1) {
+          if ((uint32_t)jj != j) continue;
+#pragma unroll
+          for (int k = 0; k < E; ++k) {
+            const int l = k ^ jj;
+            if (l > k) {
+              const bool asc = ((t * E + k) & size) == 0;
+              const T x = v[k], y = v[l];
+              const T lo = x < y ? x : y, hi = x < y ? y : x;
+              v[k] = asc ? lo : hi;
+              v[l] = asc ? hi : lo;
+            }
           }
         }
       } else if (j < 32u * E) {
@@ -260,14 +262,29 @@ __device__ __forceinline__ void bitonic_sort_regs(T *a, uint32_t n, T pad) {
 }
 
 // ascending sort of a[0..n), n a power of two; entries n.. up to the next
-// multiple of 128 (at most 512) may be overwritten with `pad`.  Not inlined:
+// multiple of blockDim.x (at most 512) may be overwritten with `pad`.  Not inlined:
 // the unrolled networks would otherwise raise the whole kernel's register count.
 template <typename T>
 __device__ __noinline__ void block_sort(T *a, uint32_t n, T pad) {
-  if (n <= kLeafThreads) bitonic_sort_regs<T, 1>(a, n, pad);
-  else if (n <= 2 * kLeafThreads) bitonic_sort_regs<T, 2>(a, n, pad);
-  else if (n <= 4 * kLeafThreads) bitonic_sort_regs<T, 4>(a, n, pad);
+  const uint32_t nt = blockDim.x;
+  if (n <= nt) bitonic_sort_regs<T, 1>(a, n, pad);
+  else if (n <= 2 * nt) bitonic_sort_regs<T, 2>(a, n, pad);
+  else if (n <= 4 * nt) bitonic_sort_regs<T, 4>(a, n, pad);
+  else if (n <= 8 * nt && n <= 512) bitonic_sort_regs<T, 8>(a, n, pad);
   else bitonic_sort_smem<T>(a, n);
+}
+
+// the SFU's exp2 and reciprocal (PTX ex2.approx.f32, rcp.approx.f32: about 2 ulp
+// and 1 ulp, subnormals kept); a score term needs no more than that
+__device__ __forceinline__ float ex2_hw(float x) {
+  float y;
+  asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_hw(float x) {
+  float y;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // squared distance with the fixed FP32 operation order of the method's reading:
@@ -348,6 +365,7 @@ template <int KMAX, typename IdxT, bool kRec>
 __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__restrict__ pts, const LeafMem &M,
                              LeafShared &S) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t NT = blockDim.x, NW = NT >> 5;  // 64 or 128 threads (execution knob)
   const uint32_t nt = lf.count;
   const denoise_params &P = A.p;
   const uint32_t lt = lanemask_lt();
@@ -366,13 +384,13 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   }
   // ---- Eq. 12: voxel occupancy (hash with warp-aggregated atomics)
   const uint32_t hcap = pow2ceil(2 * nt);  // <= the carved capacity
-  for (uint32_t i = tid; i < hcap; i += kLeafThreads) {
+  for (uint32_t i = tid; i < hcap; i += NT) {
     M.hkey[i] = kEmpty;
     M.hcnt[i] = 0;
   }
   __syncthreads();
   const float lo0 = S.lo[0], lo1 = S.lo[1], lo2 = S.lo[2], h = S.h;
-  for (uint32_t base = 0; base < nt; base += kLeafThreads) {
+  for (uint32_t base = 0; base < nt; base += NT) {
     const uint32_t i = base + tid;
     unsigned long long key = kInvalid;
     if (i < nt) {
@@ -389,7 +407,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   __syncthreads();
   // lookup, gate, compaction of P_1 (order preserved)
   const uint32_t fbeg = A.frames[lf.frame].begin;
-  for (uint32_t base = 0; base < nt; base += kLeafThreads) {
+  for (uint32_t base = 0; base < nt; base += NT) {
     const uint32_t i = base + tid;
     bool in1 = false;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -430,14 +448,14 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     __syncthreads();
     if (tid == 0) {
       uint32_t t = 0;
-      for (int ww = 0; ww < kLeafWarps; ++ww) t += S.wsum[ww];
+      for (uint32_t ww = 0; ww < NW; ++ww) t += S.wsum[ww];
       S.run += t;
     }
     __syncthreads();
   }
   const uint32_t n1 = S.run;
   if (n1 <= 1) {  // no neighbour exists: the density gate cannot keep it
-    for (uint32_t i = tid; i < n1; i += kLeafThreads) write_point<kRec>(A, M.gidx[i], 0, 0.0f, 2);
+    for (uint32_t i = tid; i < n1; i += NT) write_point<kRec>(A, M.gidx[i], 0, 0.0f, 2);
     return;
   }
   const uint32_t keff = (P.k < n1 - 1) ? P.k : n1 - 1;
@@ -445,7 +463,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     atomicAdd(&A.ctr->knn_pairs, (unsigned long long)n1 * (unsigned long long)(n1 - 1));
     atomicAdd(&A.ctr->n_p1, (unsigned long long)n1);
   }
-  if (tid == kLeafThreads - 1) {  // Eq. 14 rank (FP64, one thread), taken off the later critical path
+  if (tid == NT - 1) {  // Eq. 14 rank (FP64, one thread), taken off the later critical path
     const double pos = __dadd_rn(__ddiv_rn(__dmul_rn((double)n1, (double)P.rho_percentile), 100.0), 0.5);
     const double cc = ceil(pos);
     S.crank = (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;
@@ -474,7 +492,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     const float delta2 = __fmul_rn(S.delta, S.delta);
     const uint32_t cap = M.cap;
     const bool dbg_n = (kRec && A.use_dbg) && A.dbg.nbr, dbg_d = (kRec && A.use_dbg) && A.dbg.nbr_d2;
-    for (uint32_t qb = 0; qb < n1; qb += kLeafThreads) {
+    for (uint32_t qb = 0; qb < n1; qb += NT) {
       const uint32_t q = qb + tid;
       const bool act = q < n1;
       if (!__any_sync(0xFFFFFFFFu, act)) continue;  // whole warp idle (warp-uniform)
@@ -631,11 +649,11 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
 
   // ---- Eq. 14: exact percentile cut, as a rank cut on r_K^2 (rho decreasing in r_K)
   uint32_t *const vbuf = reinterpret_cast<uint32_t *>(M.sbuf);
-  for (uint32_t i = tid; i < sn; i += kLeafThreads) vbuf[i] = (i < n1) ? __float_as_uint(M.r2[i]) : 0xFFFFFFFFu;
+  for (uint32_t i = tid; i < sn; i += NT) vbuf[i] = (i < n1) ? __float_as_uint(M.r2[i]) : 0xFFFFFFFFu;
   __syncthreads();
   block_sort<uint32_t>(vbuf, sn, 0xFFFFFFFFu);
   const uint32_t Rb = vbuf[n1 - S.crank];
-  for (uint32_t i = tid; i < n1; i += kLeafThreads) {
+  for (uint32_t i = tid; i < n1; i += NT) {
     const uint32_t v = vbuf[i];
     if (v <= Rb && (i + 1 == n1 || vbuf[i + 1] > Rb)) S.m = i + 1;
     M.flag[i] = (__float_as_uint(M.r2[i]) <= Rb) ? 1 : 0;
@@ -687,7 +705,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     const float r2ref = S.r2ref, Lref = S.Lref;
     const float half_alpha = __fmul_rn(0.5f, P.alpha);
     const float c2 = __fdiv_rn(1.4426950408889634f, __fmul_rn(__fmul_rn(2.0f, P.sigma), P.sigma));
-    for (uint32_t i = tid; i < n1; i += kLeafThreads) {
+    for (uint32_t i = tid; i < n1; i += NT) {
       const float r2 = M.r2[i];
       const float ell = __fsub_rn(Lref, __fmul_rn(1.5f, log2f(__fdiv_rn(r2, r2ref))));  // log2(rho_i / sqrt(rho_med^2 + eps))
       M.wa[i] = __fmul_rn(half_alpha, ell);
@@ -703,7 +721,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   {
     const bool g2 = (P.gamma == 2.0f);
     const float hg = 0.5f * P.gamma, ek = P.eps_k;
-    for (uint32_t i = tid; i < n1; i += kLeafThreads) {
+    for (uint32_t i = tid; i < n1; i += NT) {
       if (!M.flag[i]) continue;
       const float4 me = M.p1[i];
       const float ai = M.wa[i], ci = M.wc[i];
@@ -728,9 +746,9 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           j = (uint32_t)nbr[(size_t)t * M.cap + i];
         }
         const float d2 = sqdist(me, M.p1[j]);
-        const float wt = exp2f(__fmaf_rn(-d2, ci, __fadd_rn(ai, M.wa[j])));  // w_den * w_dis (Eq. 17, 19)
-        const float D = g2 ? d2 : exp2f(__fmul_rn(hg, log2f(d2)));         // (d^2)^(gamma/2)
-        return __fmul_rn(wt, __frcp_rn(__fadd_rn(D, ek)));                // kernel of Eq. 20
+        const float wt = ex2_hw(__fmaf_rn(-d2, ci, __fadd_rn(ai, M.wa[j])));  // w_den * w_dis (Eq. 17, 19)
+        const float D = g2 ? d2 : exp2f(__fmul_rn(hg, log2f(d2)));          // (d^2)^(gamma/2)
+        return __fmul_rn(wt, rcp_hw(__fadd_rn(D, ek)));                    // kernel of Eq. 20
       };
       uint32_t t = 0;
       for (; t + 1 < keff; t += 2) {
@@ -747,7 +765,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   // Top-lambda: sort the keys (~F, input index); a point is kept iff its own key
   // is at most the keep_n-th smallest key (keys are unique).
   if (P.select_mode == DENOISE_SELECT_TOPRATIO) {
-    for (uint32_t i = tid; i < sn; i += kLeafThreads) {
+    for (uint32_t i = tid; i < sn; i += NT) {
       unsigned long long key = kEmpty;
       if (i < n1 && M.flag[i])
         key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | M.gidx[i];
@@ -756,19 +774,19 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     __syncthreads();
     block_sort<unsigned long long>(M.sbuf, sn, kEmpty);
     const unsigned long long cut = M.sbuf[S.keep_n - 1];
-    for (uint32_t i = tid; i < n1; i += kLeafThreads) {
+    for (uint32_t i = tid; i < n1; i += NT) {
       if (!M.flag[i]) continue;
       const unsigned long long key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | M.gidx[i];
       M.flag[i] = (key <= cut) ? 2 : 1;
     }
   } else {
-    for (uint32_t i = tid; i < n1; i += kLeafThreads)
+    for (uint32_t i = tid; i < n1; i += NT)
       if (M.flag[i]) M.flag[i] = (logf(M.F[i]) >= P.tau) ? 2 : 1;
   }
   __syncthreads();
   // ---- Eq. 22: results in input order
   const double rho_med = S.rho_med;
-  for (uint32_t i = tid; i < n1; i += kLeafThreads) {
+  for (uint32_t i = tid; i < n1; i += NT) {
     const uint32_t g = M.gidx[i];
     const uint8_t f = M.flag[i];
     if (f == 0) write_point<kRec>(A, g, 0, 0.0f, 2);
@@ -1007,13 +1025,13 @@ static int launch_k(const LeafArgs &a, int num_sms, cudaStream_t st) {
     return -1;
   cudaFuncSetAttribute(k_leaf<KMAX, kRec>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        (int)cudaSharedmemCarveoutMaxShared);
+  const int nt = (a.threads == 64) ? 64 : kLeafThreads;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf<KMAX, kRec>, kLeafThreads, smem) !=
-          cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf<KMAX, kRec>, nt, smem) != cudaSuccess ||
       per_sm < 1)
     return -1;
   if (a.ctas_per_sm > 0 && (int)a.ctas_per_sm < per_sm) per_sm = (int)a.ctas_per_sm;
-  k_leaf<KMAX, kRec><<<num_sms * per_sm, kLeafThreads, smem, st>>>(a);
+  k_leaf<KMAX, kRec><<<num_sms * per_sm, nt, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -51,7 +51,7 @@ def test_ctypes_structs_match_c_layout(native, tmp_path):
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gravdenoise.h"\n'
                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(denoise_params), sizeof(denoise_stats),'
                    ' sizeof(denoise_debug), offsetof(denoise_params, temperature), offsetof(denoise_stats, stage_ms),'
-                   ' sizeof(denoise_tuning), offsetof(denoise_tuning, leaf_smem_points));'
+                   ' sizeof(denoise_tuning), offsetof(denoise_tuning, leaf_threads));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
@@ -59,7 +59,7 @@ def test_ctypes_structs_match_c_layout(native, tmp_path):
     want = [ctypes.sizeof(native.denoise_params), ctypes.sizeof(native.denoise_stats),
             ctypes.sizeof(native.denoise_debug), native.denoise_params.temperature.offset,
             native.denoise_stats.stage_ms.offset, ctypes.sizeof(native.denoise_tuning),
-            native.denoise_tuning.leaf_smem_points.offset]
+            native.denoise_tuning.leaf_threads.offset]
     assert got == want
 
 

@@ -35,16 +35,16 @@ def test_tuned_batch_equals_per_frame(env, tmp_path):
     xyz = torch.from_numpy(np.concatenate(frames)).cuda()
     P = Params(k=24)
     cache = str(tmp_path / "tune.json")
-    best = tune_batch(xyz, offs, P, capacities=(192, 512), ctas=(0, 2), smem_points=(0, 128), reps=2,
-                      cache_path=cache)
+    best = tune_batch(xyz, offs, P, capacities=(192, 512), ctas=(0, 2), smem_points=(0, 128), threads=(0, 64),
+                      reps=2, cache_path=cache)
     assert best["leaf_capacity"] in (192, 512) and best["leaf_ctas_per_sm"] in (0, 2)
-    assert best["leaf_smem_points"] in (0, 128)
-    assert len(best["table"]) == 8
+    assert best["leaf_smem_points"] in (0, 128) and best["leaf_threads"] in (0, 64)
+    assert len(best["table"]) == 12  # 2 capacities x (2 CTA counts x 2 smem sizes at 128 threads + 2 at 64)
     assert tune_batch(xyz, offs, P, cache_path=cache)["leaf_capacity"] == best["leaf_capacity"]  # cached
     import dataclasses
     Pt = dataclasses.replace(P, leaf_capacity=best["leaf_capacity"])
     d = Denoiser(max_points=offs[-1], max_frames=len(frames))
-    d.set_tuning(best["leaf_ctas_per_sm"], best["leaf_smem_points"])
+    d.set_tuning(best["leaf_ctas_per_sm"], best["leaf_smem_points"], best["leaf_threads"])
     d.set_graphs(True)
     rb = d.run_batch(xyz, offs, Pt)
     d.set_graphs(False)
@@ -86,3 +86,25 @@ def test_results_do_not_depend_on_the_shared_memory_leaf_size(env, smem_points):
     for a, b in zip(ref, (got.mask, got.score, got.stage)):
         assert torch.equal(a, b)
     d.close()
+
+
+@pytest.mark.parametrize("threads", [64, 128])
+def test_results_do_not_depend_on_the_leaf_cta_size(env, threads):
+    """64- or 128-thread leaf CTAs: bit-identical results (LiDAR frame, K = 24,
+    capacity 256, and the dense scan subset at capacity 512)."""
+    import synth
+    from paper_2512_10386_gb300 import Denoiser, Params
+    from paper_2512_10386_gb300 import _native as N
+    for xyz, P in ((synth.lidar_frame(1001)[0], Params(k=24, leaf_capacity=256)),
+                   (synth.superquadric_scan(seed=4, n_surface=80_000)[0], Params(k=32, leaf_capacity=512))):
+        t = torch.from_numpy(xyz).cuda()
+        d = Denoiser(max_points=len(xyz))
+        ref = d.run(t, P)
+        ref = [x.clone() for x in (ref.mask, ref.score, ref.stage)]
+        d.set_tuning(0, 0, threads)
+        got = d.run(t, P)
+        for a, b in zip(ref, (got.mask, got.score, got.stage)):
+            assert torch.equal(a, b)
+        with pytest.raises(N.DenoiseError):
+            d.set_tuning(0, 0, 96)
+        d.close()
