@@ -391,12 +391,18 @@ __device__ __forceinline__ uint32_t upper_pre(const unsigned long long *kb, uint
   return lo;
 }
 
+// The leaf finder splits each front-end tile over kLeavesSplit blocks (more
+// blocks, fewer items per thread: its binary searches are latency-bound).
+constexpr uint32_t kLeavesSplit = 4;
+constexpr uint32_t kLeavesPart = kTilePts / kLeavesSplit;
+constexpr int kLeavesItems = kFrontItems / kLeavesSplit;
+static_assert(kLeavesPart == (uint32_t)kLeavesItems * kFrontThreads, "whole items per thread");
 // Largest leaf capacity whose key window fits the leaf finder's shared-memory budget
 // (the window and the found-leaf buffer stay within the default 48 KB).
-constexpr uint32_t kLeavesSmemKeys = 4800;  // 37.5 KB of keys
-constexpr uint32_t kLeavesSmemCap = (kLeavesSmemKeys - kTilePts) / 2 - 1;
-// static part: found-leaf buffer (kFrontItems x threads x 5 B) + scan words
-static_assert(kLeavesSmemKeys * 8 + kFrontItems * kFrontThreads * 5 + 64 <= 48 * 1024,
+constexpr uint32_t kLeavesSmemKeys = 5600;  // 43.75 KB of keys
+constexpr uint32_t kLeavesSmemCap = (kLeavesSmemKeys - kLeavesPart) / 2 - 1;
+// static part: found-leaf buffer (kLeavesItems x threads x 5 B) + scan words
+static_assert(kLeavesSmemKeys * 8 + kLeavesItems * kFrontThreads * 5 + 64 <= 48 * 1024,
               "leaf finder shared memory above the default 48 KB");
 
 // A sorted position i starts a leaf iff it starts its frame, or every octree
@@ -412,7 +418,12 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
                                                           uint32_t cap, int D) {
   extern __shared__ unsigned long long s_win[];
   if (ctr->status & kStFatal) return;
-  const Tile t = tiles[blockIdx.x];
+  // kLeavesSplit blocks share a tile, each taking a contiguous part of it
+  const Tile tile = tiles[blockIdx.x / kLeavesSplit];
+  const uint32_t part = blockIdx.x % kLeavesSplit;
+  Tile t = tile;
+  t.begin = min(tile.end, tile.begin + part * kLeavesPart);
+  t.end = min(tile.end, t.begin + kLeavesPart);
   const uint32_t fb = frames[t.frame].begin, fe = frames[t.frame].end;
   const unsigned long long *kb = keys;
   uint32_t koff = 0;
@@ -425,12 +436,12 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
     koff = wb;
   }
   // pass 1: each thread finds the leaves that start at its items (count, level)
-  __shared__ uint32_t s_cnt[kFrontItems][kFrontThreads];
-  __shared__ uint8_t s_lvl[kFrontItems][kFrontThreads];
+  __shared__ uint32_t s_cnt[kLeavesItems][kFrontThreads];
+  __shared__ uint8_t s_lvl[kLeavesItems][kFrontThreads];
   __shared__ uint32_t s_wsum[kFrontThreads / 32];
   __shared__ uint32_t s_base;
 #pragma unroll 1
-  for (int it = 0; it < kFrontItems; ++it) {
+  for (int it = 0; it < kLeavesItems; ++it) {
     const uint32_t i = t.begin + it * kFrontThreads + threadIdx.x;
     s_cnt[it][threadIdx.x] = 0;
     if (i >= t.end) continue;
@@ -476,7 +487,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
   // pass 2: one atomic per block reserves the block's leaf slots
   uint32_t mine = 0;
 #pragma unroll
-  for (int it = 0; it < kFrontItems; ++it) mine += s_cnt[it][threadIdx.x] ? 1u : 0u;
+  for (int it = 0; it < kLeavesItems; ++it) mine += s_cnt[it][threadIdx.x] ? 1u : 0u;
   const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t inc = mine;
   for (int o = 1; o < 32; o <<= 1) {
@@ -494,7 +505,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
   __syncthreads();
   uint32_t slot = s_base + wp + inc - mine;
 #pragma unroll
-  for (int it = 0; it < kFrontItems; ++it) {
+  for (int it = 0; it < kLeavesItems; ++it) {
     const uint32_t c = s_cnt[it][threadIdx.x];
     if (!c) continue;
     Leaf lf{};
@@ -557,10 +568,10 @@ int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t
   }
   if (ev_after_sort) cudaEventRecord(*ev_after_sort, st);
   const size_t win = (a.leaf_capacity <= kLeavesSmemCap)
-                        ? sizeof(unsigned long long) * (kTilePts + 2 * ((size_t)a.leaf_capacity + 1))
+                        ? sizeof(unsigned long long) * (kLeavesPart + 2 * ((size_t)a.leaf_capacity + 1))
                         : 0;
-  k_leaves<<<a.ntiles, kFrontThreads, win, st>>>(a.keys[cur], a.tiles, a.frames, a.leaves, a.ctr,
-                                                 a.leaf_capacity, a.max_depth);
+  k_leaves<<<a.ntiles * kLeavesSplit, kFrontThreads, win, st>>>(a.keys[cur], a.tiles, a.frames, a.leaves, a.ctr,
+                                                                a.leaf_capacity, a.max_depth);
   ++nl;
   if (launches) *launches += nl;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
