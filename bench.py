@@ -135,7 +135,7 @@ class ClockSampler:
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("gd_leaf.cu", "gd_common.cuh"):
+    for f in ("gd_leaf.cu", "gd_leaf_kernel.cuh", "gd_common.cuh"):
         with open(os.path.join(ROOT, "paper_2512_10386_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -171,6 +171,8 @@ uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit);
 // largest-first leaf order; must precede launch_leaf on the same stream.
 int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches);
 int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches);
+// the recording instantiation (debug / training outputs), in its own translation unit
+int launch_leaf_rec(const LeafArgs &a, int num_sms, cudaStream_t st);
 
 struct BackArgs {
   TrainCache train;

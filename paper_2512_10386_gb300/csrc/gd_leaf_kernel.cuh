@@ -1,0 +1,891 @@
+// gd_leaf_kernel.cuh -- device code of the fused per-leaf kernel, shared by the
+// two translation units that instantiate it (gd_leaf.cu: the plain path;
+// gd_leaf_rec.cu: the instantiation that also writes debug / training tensors).
+// Split so the two sets of instantiations compile in parallel.
+#pragma once
+
+#include "gd_common.cuh"
+
+namespace gd {
+
+constexpr int kLeafThreads = 128;
+constexpr int kLeafWarps = kLeafThreads / 32;
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr unsigned long long kInvalid = ~0ull - 1ull;
+constexpr uint32_t kPend = 8;  // parking slots per lane: a warp merges before any lane could overflow
+// the sort buffer also holds the parked candidates during the kNN
+constexpr size_t kPendBytes = (size_t)kPend * kLeafThreads * sizeof(float);
+
+__host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ __forceinline__ uint32_t pow2ceil(uint32_t x) {
+  uint32_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Per-leaf working arrays: shared memory (small leaves) or global spill (large).
+struct LeafMem {
+  float4 *p1;                // [cap] P_1 points; w = input index (bits)
+  unsigned long long *hkey;  // [hcap] voxel hash keys
+  uint32_t *hcnt;            // [hcap] voxel occupancy
+  unsigned long long *sbuf;  // [scap] sort buffer
+  float *r2, *wa, *wc, *F;   // [cap] per P_1 position
+  uint32_t *gidx;            // [cap] global input index per P_1 position
+  uint8_t *flag;             // [cap] 0 removed by density gate, 1 scored, 2 kept
+  void *nbr;                 // neighbour positions: see nb_bits (shared memory) or [KMAX][cap] u32 (global)
+  uint32_t hcap, scap, cap;
+};
+
+// Neighbour table of the shared-memory path: query q owns nb_words(cap, kmax)
+// consecutive 32-bit words holding its neighbour positions as nb_bits(cap)-bit
+// fields, rank t at bit t * nb_bits (a 512-point leaf needs 9 bits, not 16).
+// The packing keeps a 512-point, K = 32 CTA under 45 KB: 5 CTAs per SM.
+__host__ __device__ __forceinline__ uint32_t nb_bits(uint32_t cap) {
+  uint32_t b = 1;
+  while ((1u << b) < cap) ++b;
+  return b;
+}
+// an odd word count per query keeps the lanes of a warp on distinct banks
+__host__ __device__ __forceinline__ uint32_t nb_words(uint32_t cap, int kmax) {
+  return (((uint32_t)kmax * nb_bits(cap) + 31u) / 32u) | 1u;
+}
+
+// Layout of the per-leaf arrays.  `alias_head` bytes at the start (the TMA
+// landing zone of the leaf's raw points) are shared with the hash table and
+// the neighbour table, whose lifetimes do not overlap with it.
+template <typename IdxT>
+__host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t cap, int kmax, LeafMem *m,
+                                                 size_t head_bytes) {
+  const uint32_t hcap = pow2ceil(2 * cap), scap = pow2ceil(cap);
+  // region A: max(raw points + hash table, neighbour table)
+  const size_t hash_off = al16(head_bytes);
+  const size_t hash_end = hash_off + al16((size_t)hcap * 8) + al16((size_t)hcap * 4);
+  const size_t nbr_bytes = (sizeof(IdxT) == 2) ? al16((size_t)cap * nb_words(cap, kmax) * 4)
+                                               : al16((size_t)cap * kmax * sizeof(IdxT));
+  size_t off = hash_end > nbr_bytes ? hash_end : nbr_bytes;
+  off = al16(off);
+  if (m) {
+    m->hkey = (unsigned long long *)(base + hash_off);
+    m->hcnt = (uint32_t *)(base + hash_off + al16((size_t)hcap * 8));
+    m->nbr = (void *)base;
+    m->hcap = hcap;
+    m->scap = scap;
+    m->cap = cap;
+  }
+  size_t o = off;
+  auto take = [&](size_t bytes) { size_t r = o; o = al16(o + bytes); return r; };
+  const size_t sbytes = (size_t)scap * 8 > kPendBytes ? (size_t)scap * 8 : kPendBytes;
+  const size_t p1 = take((size_t)cap * 16), sb = take(sbytes);
+  const size_t r2 = take((size_t)cap * 4), wa = take((size_t)cap * 4), wc = take((size_t)cap * 4);
+  const size_t F = take((size_t)cap * 4), gi = take((size_t)cap * 4);
+  const size_t fl = take((size_t)cap);
+  if (m) {
+    m->p1 = (float4 *)(base + p1);
+    m->sbuf = (unsigned long long *)(base + sb);
+    m->r2 = (float *)(base + r2);
+    m->wa = (float *)(base + wa);
+    m->wc = (float *)(base + wc);
+    m->F = (float *)(base + F);
+    m->gidx = (uint32_t *)(base + gi);
+    m->flag = (uint8_t *)(base + fl);
+  }
+  return o;
+}
+
+struct LeafShared {
+  uint32_t leaf;
+  uint32_t n1, keff, m, keep_n, run;
+  uint32_t crank;  // Eq. 14 cut rank c, from the top of the ascending r^2 order
+  float lo[3], h, delta, r2ref, Lref;
+  double rho_med;
+  uint32_t wsum[kLeafWarps];
+  uint32_t red[kLeafWarps][6];
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+// Eq. 11 cube root: u = m 2^e (frexp), y0 = 2^floor(e/3), ten Newton steps
+// y <- y - (y*y*y - u) / (3*(y*y)), every operation rounded in FP64.  The step
+// is a fixed function of y, so once it reaches a fixed point, or a 2-cycle, the
+// tenth iterate is known and the remaining steps are skipped (same bits as all
+// ten; FP64 issue is slow on this part).
+__device__ __forceinline__ double cbrt_spec(double u) {
+  int e = 0;
+  (void)frexp(u, &e);
+  const int k = (e >= 0) ? e / 3 : -((-e + 2) / 3);
+  double y = ldexp(1.0, k), prev = 0.0;  // y = y_i, prev = y_(i-1)
+#pragma unroll 1
+  for (int it = 0; it < 10; ++it) {
+    const double y2 = __dmul_rn(y, y);
+    const double y3 = __dmul_rn(y2, y);
+    const double yn = __dsub_rn(y, __ddiv_rn(__dsub_rn(y3, u), __dmul_rn(3.0, y2)));  // y_(it+1)
+    if (yn == y) return y;                                  // fixed point: y_10 = y_it
+    if (it > 0 && yn == prev) return (it & 1) ? yn : y;     // y_(it-1), y_it alternate: y_10
+    prev = y;
+    y = yn;
+  }
+  return y;
+}
+
+__device__ __forceinline__ uint32_t vox_index(float x, float lo, float h) {
+  const float f = floorf(__fdiv_rn(__fsub_rn(x, lo), h));
+  return (f < 2097151.0f) ? (uint32_t)f : kQMax;
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t hash_insert(unsigned long long *hk, uint32_t hcap, unsigned long long key,
+                                                Counters *ctr) {
+  const uint32_t mask = hcap - 1;
+  uint32_t s = (uint32_t)mix64(key) & mask;
+  for (uint32_t probe = 0; probe < hcap; ++probe) {
+    const unsigned long long prev = atomicCAS(hk + s, kEmpty, key);
+    if (prev == kEmpty || prev == key) return s;
+    s = (s + 1) & mask;
+  }
+  atomicOr(&ctr->status, kStInternal);
+  return s;
+}
+
+__device__ __forceinline__ uint32_t hash_find(const unsigned long long *hk, uint32_t hcap,
+                                              unsigned long long key) {
+  const uint32_t mask = hcap - 1;
+  uint32_t s = (uint32_t)mix64(key) & mask;
+  for (uint32_t probe = 0; probe < hcap; ++probe) {
+    if (hk[s] == key) return s;
+    s = (s + 1) & mask;
+  }
+  return 0xFFFFFFFFu;
+}
+
+// Ascending bitonic sort of a[0..n) (n a power of two) by the whole block, one
+// compare-exchange stage per barrier: the general form, for any n.
+template <typename T>
+__device__ void bitonic_sort_smem(T *a, uint32_t n) {
+  for (uint32_t k = 2; k <= n; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const T x = a[i], y = a[l];
+          const bool asc = (i & k) == 0;
+          if ((x > y) == asc) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// The same network on N = blockDim.x * E elements held in registers: thread t owns
+// elements t*E .. t*E+E-1 (a padded with `pad` from n up to N).  A stage whose
+// partner distance j is below E stays in the thread, below 32*E it is a warp
+// shuffle, and only the stages with j >= 32*E go through shared memory (3 of
+// the 45 stages at N = 512 with 128 threads), so the sort needs a handful of
+// barriers instead of one per stage.  Writes the sorted N elements back to a
+// (a must hold N).
+template <typename T, int E>
+__device__ __forceinline__ void bitonic_sort_regs(T *a, uint32_t n, T pad) {
+  const uint32_t N = blockDim.x * E;
+  const uint32_t t = threadIdx.x;
+  T v[E];
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const uint32_t e = t * E + k;
+    v[k] = (e < n) ? a[e] : pad;
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (uint32_t size = 2; size <= N; size <<= 1) {
+#pragma unroll 1
+    for (uint32_t j = size >> 1; j > 0; j >>= 1) {
+      if (j < (uint32_t)E) {  // partners inside the thread (register indices fixed per jj)
+#pragma unroll
+        for (int jj = 1; jj < E; jj <<= 1) {
+          if ((uint32_t)jj != j) continue;
+#pragma unroll
+          for (int k = 0; k < E; ++k) {
+            const int l = k ^ jj;
+            if (l > k) {
+              const bool asc = ((t * E + k) & size) == 0;
+              const T x = v[k], y = v[l];
+              const T lo = x < y ? x : y, hi = x < y ? y : x;
+              v[k] = asc ? lo : hi;
+              v[l] = asc ? hi : lo;
+            }
+          }
+        }
+      } else if (j < 32u * E) {
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+          const uint32_t e = t * E + k;
+          const T y = __shfl_xor_sync(0xFFFFFFFFu, v[k], j / E);
+          const bool take_min = ((e & j) == 0) == ((e & size) == 0);
+          v[k] = take_min ? (v[k] < y ? v[k] : y) : (v[k] < y ? y : v[k]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < E; ++k) a[t * E + k] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+          const uint32_t e = t * E + k;
+          const T y = a[e ^ j];
+          const bool take_min = ((e & j) == 0) == ((e & size) == 0);
+          v[k] = take_min ? (v[k] < y ? v[k] : y) : (v[k] < y ? y : v[k]);
+        }
+        __syncthreads();
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < E; ++k) a[t * E + k] = v[k];
+  __syncthreads();
+}
+
+// ascending sort of a[0..n), n a power of two; entries n.. up to the next
+// multiple of blockDim.x (at most 512) may be overwritten with `pad`.  Not inlined:
+// the unrolled networks would otherwise raise the whole kernel's register count.
+template <typename T>
+__device__ __noinline__ void block_sort(T *a, uint32_t n, T pad) {
+  const uint32_t nt = blockDim.x;
+  if (n <= nt) bitonic_sort_regs<T, 1>(a, n, pad);
+  else if (n <= 2 * nt) bitonic_sort_regs<T, 2>(a, n, pad);
+  else if (n <= 4 * nt) bitonic_sort_regs<T, 4>(a, n, pad);
+  else if (n <= 8 * nt && n <= 512) bitonic_sort_regs<T, 8>(a, n, pad);
+  else bitonic_sort_smem<T>(a, n);
+}
+
+// the SFU's exp2 and reciprocal (PTX ex2.approx.f32, rcp.approx.f32: about 2 ulp
+// and 1 ulp, subnormals kept); a score term needs no more than that
+__device__ __forceinline__ float ex2_hw(float x) {
+  float y;
+  asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_hw(float x) {
+  float y;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// squared distance with the fixed FP32 operation order of the method's reading:
+// dx = x_j - x_i;  d^2 = fma(dz, dz, fma(dy, dy, dx*dx))
+__device__ __forceinline__ float sqdist(const float4 &a, const float4 &b) {
+  const float dx = __fsub_rn(b.x, a.x), dy = __fsub_rn(b.y, a.y), dz = __fsub_rn(b.z, a.z);
+  return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// ---------------------------------------------------------------------------
+// per-thread sorted register lists (all indices compile-time)
+// ---------------------------------------------------------------------------
+// ascending bitonic sort
+template <int N>
+__device__ __forceinline__ void regsort_f(float (&L)[N]) {
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const float a = L[i], b = L[l];
+          const bool asc = (i & k) == 0;
+          L[i] = asc ? fminf(a, b) : fmaxf(a, b);
+          L[l] = asc ? fmaxf(a, b) : fminf(a, b);
+        }
+      }
+    }
+  }
+}
+
+// Merge the lane's np (<= kPend) parked values (column `tid` of `pend`) into the
+// ascending list L: sort them (padded with +inf), take min(L[KMAX-kPend+i],
+// B[kPend-1-i]) (a bitonic sequence holding the KMAX smallest), then restore the
+// order with a half-cleaner cascade.
+template <int KMAX>
+__device__ __forceinline__ void merge_pending(float (&L)[KMAX], const float *pend, uint32_t np, uint32_t tid) {
+  float B[kPend];
+#pragma unroll
+  for (int i = 0; i < (int)kPend; ++i) B[i] = ((uint32_t)i < np) ? pend[i * kLeafThreads + tid] : INFINITY;
+  regsort_f<kPend>(B);
+#pragma unroll
+  for (int i = 0; i < (int)kPend; ++i) L[KMAX - kPend + i] = fminf(L[KMAX - kPend + i], B[kPend - 1 - i]);
+#pragma unroll
+  for (int j = KMAX / 2; j > 0; j >>= 1) {
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+      if ((i & j) == 0) {
+        const float a = L[i], b = L[i + j];
+        L[i] = fminf(a, b);
+        L[i + j] = fmaxf(a, b);
+      }
+    }
+  }
+}
+
+template <bool kRec>
+__device__ __forceinline__ void write_point(const LeafArgs &A, uint32_t g, uint8_t mk, float sc, uint8_t st) {
+  if (g >= A.n) {  // cannot happen with a consistent sort; never write out of bounds
+    atomicOr(&A.ctr->status, kStInternal);
+    return;
+  }
+  if (A.mask) A.mask[g] = mk;
+  if (A.score) A.score[g] = sc;
+  if (A.stage) A.stage[g] = st;
+  if (kRec && A.use_train) {
+    A.train.stage[g] = st;
+    A.train.F[g] = sc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one leaf
+// ---------------------------------------------------------------------------
+template <int KMAX, typename IdxT, bool kRec>
+__device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__restrict__ pts, const LeafMem &M,
+                             LeafShared &S) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t NT = blockDim.x, NW = NT >> 5;  // 64 or 128 threads (execution knob)
+  const uint32_t nt = lf.count;
+  const denoise_params &P = A.p;
+  const uint32_t lt = lanemask_lt();
+  IdxT *nbr = (IdxT *)M.nbr;
+  constexpr bool kPacked = sizeof(IdxT) == 2;  // shared-memory path: bit-packed neighbour table
+  const uint32_t nbB = nb_bits(M.cap), nbW = nb_words(M.cap, KMAX);
+
+  // ---- Eq. 10-11: the leaf's box origin and voxel size h come from the prep kernel
+  if (tid == 0) {
+    S.lo[0] = lf.lo[0];
+    S.lo[1] = lf.lo[1];
+    S.lo[2] = lf.lo[2];
+    S.h = lf.h;
+    S.delta = A.frames[lf.frame].delta;
+    S.run = 0;
+  }
+  // ---- Eq. 12: voxel occupancy (hash with warp-aggregated atomics)
+  const uint32_t hcap = pow2ceil(2 * nt);  // <= the carved capacity
+  for (uint32_t i = tid; i < hcap; i += NT) {
+    M.hkey[i] = kEmpty;
+    M.hcnt[i] = 0;
+  }
+  __syncthreads();
+  const float lo0 = S.lo[0], lo1 = S.lo[1], lo2 = S.lo[2], h = S.h;
+  for (uint32_t base = 0; base < nt; base += NT) {
+    const uint32_t i = base + tid;
+    unsigned long long key = kInvalid;
+    if (i < nt) {
+      const float4 p = pts[i];
+      key = ((unsigned long long)vox_index(p.x, lo0, h) << 42) |
+            ((unsigned long long)vox_index(p.y, lo1, h) << 21) | (unsigned long long)vox_index(p.z, lo2, h);
+    }
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
+    if (i < nt && (peers & lt) == 0) {
+      const uint32_t s = hash_insert(M.hkey, hcap, key, A.ctr);
+      atomicAdd(M.hcnt + s, (uint32_t)__popc(peers));
+    }
+  }
+  __syncthreads();
+  // lookup, gate, compaction of P_1 (order preserved)
+  const uint32_t fbeg = A.frames[lf.frame].begin;
+  for (uint32_t base = 0; base < nt; base += NT) {
+    const uint32_t i = base + tid;
+    bool in1 = false;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t g = 0;
+    if (i < nt) {
+      p = pts[i];
+      g = __float_as_uint(p.w);
+      if (g >= A.n) {
+        atomicOr(&A.ctr->status, kStInternal);
+        g = 0;
+      }
+      const unsigned long long key = ((unsigned long long)vox_index(p.x, lo0, h) << 42) |
+                                     ((unsigned long long)vox_index(p.y, lo1, h) << 21) |
+                                     (unsigned long long)vox_index(p.z, lo2, h);
+      const uint32_t s = hash_find(M.hkey, hcap, key);
+      const uint32_t c = (s == 0xFFFFFFFFu) ? 0u : M.hcnt[s];
+      in1 = c >= P.min_vox_count;
+      if ((kRec && A.use_dbg)) {
+        if (A.dbg.vox_count) A.dbg.vox_count[g] = c;
+        if (A.dbg.leaf_start) A.dbg.leaf_start[g] = lf.start - fbeg;
+        if (A.dbg.leaf_count) A.dbg.leaf_count[g] = nt;
+        if (A.dbg.leaf_h) A.dbg.leaf_h[g] = h;
+        if (A.dbg.leaf_rho_med) A.dbg.leaf_rho_med[g] = 0.0;
+        if (A.dbg.r2) A.dbg.r2[g] = 0.0f;
+      }
+      if (!in1) write_point<kRec>(A, g, 0, 0.0f, 1);
+    }
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, in1);
+    if (lane == 0) S.wsum[w] = __popc(bal);
+    __syncthreads();
+    uint32_t off = S.run;
+    for (uint32_t ww = 0; ww < w; ++ww) off += S.wsum[ww];
+    if (in1) {
+      const uint32_t pos = off + __popc(bal & lt);
+      M.p1[pos] = p;
+      M.gidx[pos] = g;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t t = 0;
+      for (uint32_t ww = 0; ww < NW; ++ww) t += S.wsum[ww];
+      S.run += t;
+    }
+    __syncthreads();
+  }
+  const uint32_t n1 = S.run;
+  if (n1 <= 1) {  // no neighbour exists: the density gate cannot keep it
+    for (uint32_t i = tid; i < n1; i += NT) write_point<kRec>(A, M.gidx[i], 0, 0.0f, 2);
+    return;
+  }
+  const uint32_t keff = (P.k < n1 - 1) ? P.k : n1 - 1;
+  if (tid == 0) {
+    atomicAdd(&A.ctr->knn_pairs, (unsigned long long)n1 * (unsigned long long)(n1 - 1));
+    atomicAdd(&A.ctr->n_p1, (unsigned long long)n1);
+  }
+  if (tid == NT - 1) {  // Eq. 14 rank (FP64, one thread), taken off the later critical path
+    const double pos = __dadd_rn(__ddiv_rn(__dmul_rn((double)n1, (double)P.rho_percentile), 100.0), 0.5);
+    const double cc = ceil(pos);
+    S.crank = (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;
+  }
+  const uint32_t sn = pow2ceil(n1);
+
+  // ---- kNN on P_1 (excluding self), order by (d^2, input index): one thread per query.
+  // Phase A finds theta, the k_eff-th smallest d^2, in a sorted register list of
+  // FP32 values (placeholders -1 fill the unused KMAX - k_eff slots).  The list
+  // is seeded with the k_eff Morton-order neighbours of the query (window
+  // [ws, we]) and sorted once by a register bitonic network.  The scan then
+  // broadcasts the other candidates from shared memory to the warp, four per
+  // step (four independent distance chains); a lane whose candidate beats its
+  // current k-th value parks it in its column of a small shared buffer, and
+  // once some lane could overflow its kPend slots at the next step the warp
+  // merges the parked values into the lists (sort of kPend values + bitonic
+  // merge), so the list update is paid once per batch, not per insertion.
+  // Phase B rescans all candidates (four per step): every d^2 < theta is kept;
+  // the candidates at exactly theta are counted and, when exactly as many ties
+  // as needed exist, all kept.  Otherwise (exact lattices, duplicates) extra
+  // scans take the ties in input-index order.  The set is the k_eff smallest by
+  // (d^2, input index), as with a full sort.
+  {
+    // parked candidates live in the sort buffer, idle during the kNN (kPend columns of kLeafThreads)
+    float *const pend = reinterpret_cast<float *>(M.sbuf);
+    const float delta2 = __fmul_rn(S.delta, S.delta);
+    const uint32_t cap = M.cap;
+    const bool dbg_n = (kRec && A.use_dbg) && A.dbg.nbr, dbg_d = (kRec && A.use_dbg) && A.dbg.nbr_d2;
+    for (uint32_t qb = 0; qb < n1; qb += NT) {
+      const uint32_t q = qb + tid;
+      const bool act = q < n1;
+      if (!__any_sync(0xFFFFFFFFu, act)) continue;  // whole warp idle (warp-uniform)
+      const uint32_t qq = act ? q : n1 - 1;          // idle lanes shadow a real query, results discarded
+      const float4 me = M.p1[qq];
+      const uint32_t j0 = qb + w * 32;               // < n1: lane 0 of a busy warp is busy
+      const uint32_t half = keff / 2;
+      uint32_t ws = (qq > half) ? qq - half : 0u;
+      if (ws > n1 - 1 - keff) ws = n1 - 1 - keff;
+      const uint32_t we = ws + keff;
+      float L[KMAX];
+#pragma unroll
+      for (int sl = 0; sl < KMAX; ++sl) {
+        const int r = sl - (KMAX - (int)keff);
+        float v = -1.0f;
+        if (r >= 0) {
+          uint32_t j = ws + (uint32_t)r;
+          if (j >= qq) ++j;
+          v = sqdist(me, M.p1[j]);
+        }
+        L[sl] = v;
+      }
+      regsort_f<KMAX>(L);
+      uint32_t np = 0;
+      for (uint32_t pass = 0; pass < 2; ++pass) {
+        const uint32_t jb = pass == 0 ? j0 : 0u, je = pass == 0 ? n1 : j0;
+        for (uint32_t j = jb; j < je; j += 4) {
+          uint32_t jj[4];
+          float dd[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const bool ok = j + u < je;
+            jj[u] = ok ? j + u : j;
+            dd[u] = ok ? sqdist(me, M.p1[jj[u]]) : INFINITY;
+          }
+          const float thr = L[KMAX - 1];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (dd[u] < thr && (jj[u] < ws || jj[u] > we)) {
+              pend[np * kLeafThreads + tid] = dd[u];
+              ++np;
+            }
+          }
+          if (__any_sync(0xFFFFFFFFu, np + 4 > kPend)) {
+            merge_pending<KMAX>(L, pend, np, tid);
+            np = 0;
+          }
+        }
+      }
+      merge_pending<KMAX>(L, pend, np, tid);
+      const float theta = L[KMAX - 1];
+      uint32_t below = 0;
+#pragma unroll
+      for (int sl = 0; sl < KMAX; ++sl) below += (L[sl] >= 0.0f && L[sl] < theta) ? 1u : 0u;
+      const uint32_t ties_needed = keff - below;  // >= 1: theta itself is a candidate
+      const uint32_t gq = M.gidx[qq];
+      // Record neighbour t of this query (position npos, input index g, distance d2).
+      // Ranks come in order t = 0, 1, ...: the packed table is filled through a
+      // bit buffer, one word store per 32 bits.
+      uint32_t *const nbw = reinterpret_cast<uint32_t *>(M.nbr) + (size_t)qq * nbW;
+      unsigned long long nb_acc = 0;
+      uint32_t nb_n = 0, nb_w = 0;
+      auto emit = [&](uint32_t t, uint32_t npos, uint32_t g, float d2) {
+        if constexpr (kPacked) {
+          nb_acc |= (unsigned long long)npos << nb_n;
+          nb_n += nbB;
+          if (nb_n >= 32) {
+            nbw[nb_w++] = (uint32_t)nb_acc;
+            nb_acc >>= 32;
+            nb_n -= 32;
+          }
+        } else {
+          nbr[(size_t)t * cap + qq] = (IdxT)npos;
+        }
+        if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = g;
+        if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = d2;
+        if ((kRec && A.use_train)) {
+          A.train.nbr[(size_t)gq * P.k + t] = g;
+          A.train.nd2[(size_t)gq * P.k + t] = d2;
+        }
+      };
+      // every d^2 < theta is a neighbour; the ntie candidates at exactly theta are
+      // counted and the position of the last one kept (common case: one tie, the
+      // k_eff-th neighbour itself)
+      uint32_t a = 0, ntie = 0, tp = 0;
+      for (uint32_t j = 0; j < n1; j += 4) {
+        float4 cv[4];
+        float dv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          cv[u] = M.p1[(j + u < n1) ? j + u : j];
+          dv[u] = sqdist(me, cv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t ju = j + u;
+          if (ju < n1 && ju != qq) {
+            if (dv[u] < theta) {
+              if (act && a < keff) emit(a, ju, __float_as_uint(cv[u].w), dv[u]);
+              ++a;
+            } else if (dv[u] == theta) {
+              ++ntie;
+              tp = ju;
+            }
+          }
+        }
+      }
+      if (act && a != below) atomicOr(&A.ctr->status, kStInternal);  // the two phases must agree
+      // ties: with exactly ties_needed of them all are taken, otherwise the
+      // ties_needed smallest input indices (rare: exact lattices, duplicates)
+      const bool all_ties = ntie == ties_needed;
+      if (act && all_ties && ties_needed == 1) emit(below, tp, __float_as_uint(M.p1[tp].w), theta);
+      // one scan emits every tie; or one scan per tie picks the smallest index above the last
+      const uint32_t rounds = !act ? 0u : all_ties ? (ties_needed > 1 ? 1u : 0u) : ties_needed;
+      const uint32_t max_rounds = __reduce_max_sync(0xFFFFFFFFu, rounds);
+      uint32_t last = 0, slot = below;
+      for (uint32_t r = 0; r < max_rounds; ++r) {
+        uint32_t bg = 0xFFFFFFFFu, bp = 0;
+        for (uint32_t j = 0; j < n1; ++j) {
+          const float4 cj = M.p1[j];
+          const float d2 = sqdist(me, cj);
+          if (r >= rounds || j == qq || d2 != theta) continue;
+          const uint32_t g = __float_as_uint(cj.w);
+          if (all_ties) {
+            if (slot < keff) emit(slot++, j, g, theta);
+          } else if ((r == 0 || g > last) && g < bg) {
+            bg = g;
+            bp = j;
+          }
+        }
+        if (r < rounds && !all_ties && slot < keff) {
+          emit(slot++, bp, bg, theta);
+          last = bg;
+        }
+      }
+      if (kPacked && act && nb_n > 0) nbw[nb_w] = (uint32_t)nb_acc;  // last partial word
+      if (act) {
+        for (uint32_t t = keff; t < P.k; ++t) {
+          if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
+          if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = 0.0f;
+          if ((kRec && A.use_train)) {
+            A.train.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
+            A.train.nd2[(size_t)gq * P.k + t] = 0.0f;
+          }
+        }
+        const float rt = (theta < delta2) ? delta2 : theta;
+        M.r2[qq] = rt;
+        if ((kRec && A.use_dbg) && A.dbg.r2) A.dbg.r2[gq] = rt;
+        if ((kRec && A.use_train)) A.train.r2[gq] = rt;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- Eq. 14: exact percentile cut, as a rank cut on r_K^2 (rho decreasing in r_K)
+  uint32_t *const vbuf = reinterpret_cast<uint32_t *>(M.sbuf);
+  for (uint32_t i = tid; i < sn; i += NT) vbuf[i] = (i < n1) ? __float_as_uint(M.r2[i]) : 0xFFFFFFFFu;
+  __syncthreads();
+  block_sort<uint32_t>(vbuf, sn, 0xFFFFFFFFu);
+  const uint32_t Rb = vbuf[n1 - S.crank];
+  for (uint32_t i = tid; i < n1; i += NT) {
+    const uint32_t v = vbuf[i];
+    if (v <= Rb && (i + 1 == n1 || vbuf[i + 1] > Rb)) S.m = i + 1;
+    M.flag[i] = (__float_as_uint(M.r2[i]) <= Rb) ? 1 : 0;
+  }
+  __syncthreads();
+  const uint32_t m = S.m;
+  // ---- Eq. 16: median density over P_2 and the per-leaf constants of the score.
+  // With rho(r2) = k_eff / (4/3 pi r2^1.5), the score needs
+  // ell_i = log2(rho_i / sqrt(rho_med^2 + eps_rho)) = Lref - 1.5 log2(r2_i / r2ref)
+  // with r2ref the lower-middle r2 of P_2 and Lref = log2(rho(r2ref)) -
+  // log2(rho_med) - 0.5 log2(1 + eps_rho / rho_med^2).  Every term is a log2 of a
+  // ratio near 1 (or the eps correction), evaluated in FP32 without overflow.
+  if (tid == 0) {
+    const uint32_t mid = (m - 1) / 2;
+    const float ra = __uint_as_float(vbuf[mid]);
+    // log2(rho(ra) / rho_med): 0 for odd m, 1 - log2(1 + (ra / rb)^1.5) for even m
+    float lr = 0.0f;
+    float rb = ra;
+    if (!(m & 1u)) {
+      rb = __uint_as_float(vbuf[m / 2]);
+      const float t = __fdiv_rn(ra, rb);
+      lr = __fsub_rn(1.0f, log2f(__fadd_rn(1.0f, __fmul_rn(t, sqrtf(t)))));
+    }
+    // log2(rho_med) = log2(rho(ra)) - lr, with log2(rho(ra)) = log2(k_eff) - log2(4/3 pi) - 1.5 log2(ra)
+    const float l_rho_a =
+        __fsub_rn(__fsub_rn(log2f((float)keff), 2.0665336287511624f), __fmul_rn(1.5f, log2f(ra)));
+    const float l_med = __fsub_rn(l_rho_a, lr);
+    float corr = 0.0f;
+    if (P.eps_rho > 0.0f) {
+      const float lx = __fsub_rn(log2f(P.eps_rho), __fmul_rn(2.0f, l_med));  // log2(eps_rho / rho_med^2)
+      corr = (lx > 100.0f) ? __fmul_rn(0.5f, lx) : __fmul_rn(0.5f, log2f(__fadd_rn(1.0f, exp2f(lx))));
+    }
+    S.r2ref = ra;
+    S.Lref = __fsub_rn(lr, corr);
+    S.keep_n = (uint32_t)ceil((double)P.lambda * (double)m);
+    if (S.keep_n > m) S.keep_n = m;
+    atomicAdd(&A.ctr->n_p2, (unsigned long long)m);
+    if ((kRec && A.use_dbg) && A.dbg.leaf_rho_med) {  // exact FP64 value for the parity output only
+      const double k43pi = (4.0 / 3.0) * 3.14159265358979323846;
+      auto rho_of = [&](float r2) {
+        const double rr = (double)r2;
+        return (double)keff / __dmul_rn(k43pi, __dmul_rn(rr, sqrt(rr)));
+      };
+      S.rho_med = (m & 1u) ? rho_of(ra) : 0.5 * (rho_of(__uint_as_float(vbuf[m / 2 - 1])) + rho_of(rb));
+    }
+  }
+  __syncthreads();
+  {
+    const float r2ref = S.r2ref, Lref = S.Lref;
+    const float half_alpha = __fmul_rn(0.5f, P.alpha);
+    const float c2 = __fdiv_rn(1.4426950408889634f, __fmul_rn(__fmul_rn(2.0f, P.sigma), P.sigma));
+    for (uint32_t i = tid; i < n1; i += NT) {
+      const float r2 = M.r2[i];
+      const float ell = __fsub_rn(Lref, __fmul_rn(1.5f, log2f(__fdiv_rn(r2, r2ref))));  // log2(rho_i / sqrt(rho_med^2 + eps))
+      M.wa[i] = __fmul_rn(half_alpha, ell);
+      M.wc[i] = __fdiv_rn(c2, r2);
+      if ((kRec && A.use_train)) A.train.ell[M.gidx[i]] = ell;
+    }
+  }
+  __syncthreads();
+  // ---- Eq. 15-21: dual-weight gravitational score of every P_2 point.  Every FP32
+  // operation of the score, and of the per-leaf and per-point constants above, is an
+  // explicit round-to-nearest intrinsic: no contraction is left to the compiler, so
+  // the shared-memory and global-memory instantiations give bit-identical scores.
+  {
+    const bool g2 = (P.gamma == 2.0f);
+    const float hg = 0.5f * P.gamma, ek = P.eps_k;
+    for (uint32_t i = tid; i < n1; i += NT) {
+      if (!M.flag[i]) continue;
+      const float4 me = M.p1[i];
+      const float ai = M.wa[i], ci = M.wc[i];
+      // two neighbours per step into two partial sums (independent chains),
+      // F = even-rank terms + odd-rank terms
+      float F0 = 0.0f, F1 = 0.0f;
+      const uint32_t *nbr_i = reinterpret_cast<const uint32_t *>(M.nbr) + (size_t)i * nbW;
+      unsigned long long r_acc = 0;
+      uint32_t r_n = 0;
+      const uint32_t r_mask = (1u << nbB) - 1u;
+      auto term = [&](uint32_t t) {  // called for t = 0, 1, ... in order
+        uint32_t j;
+        if constexpr (kPacked) {
+          if (r_n < nbB) {
+            r_acc |= (unsigned long long)(*nbr_i++) << r_n;
+            r_n += 32;
+          }
+          j = (uint32_t)r_acc & r_mask;
+          r_acc >>= nbB;
+          r_n -= nbB;
+        } else {
+          j = (uint32_t)nbr[(size_t)t * M.cap + i];
+        }
+        const float d2 = sqdist(me, M.p1[j]);
+        const float wt = ex2_hw(__fmaf_rn(-d2, ci, __fadd_rn(ai, M.wa[j])));  // w_den * w_dis (Eq. 17, 19)
+        const float D = g2 ? d2 : exp2f(__fmul_rn(hg, log2f(d2)));          // (d^2)^(gamma/2)
+        return __fmul_rn(wt, rcp_hw(__fadd_rn(D, ek)));                    // kernel of Eq. 20
+      };
+      uint32_t t = 0;
+      for (; t + 1 < keff; t += 2) {
+        const float e0 = term(t), e1 = term(t + 1);
+        F0 = __fadd_rn(F0, e0);
+        F1 = __fadd_rn(F1, e1);
+      }
+      if (t < keff) F0 = __fadd_rn(F0, term(t));
+      M.F[i] = __fadd_rn(F0, F1);
+    }
+  }
+  __syncthreads();
+  // ---- selection: Top-lambda per leaf by (F desc, input index asc), or ln F >= tau.
+  // Top-lambda: sort the keys (~F, input index); a point is kept iff its own key
+  // is at most the keep_n-th smallest key (keys are unique).
+  if (P.select_mode == DENOISE_SELECT_TOPRATIO) {
+    for (uint32_t i = tid; i < sn; i += NT) {
+      unsigned long long key = kEmpty;
+      if (i < n1 && M.flag[i])
+        key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | M.gidx[i];
+      M.sbuf[i] = key;
+    }
+    __syncthreads();
+    block_sort<unsigned long long>(M.sbuf, sn, kEmpty);
+    const unsigned long long cut = M.sbuf[S.keep_n - 1];
+    for (uint32_t i = tid; i < n1; i += NT) {
+      if (!M.flag[i]) continue;
+      const unsigned long long key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | M.gidx[i];
+      M.flag[i] = (key <= cut) ? 2 : 1;
+    }
+  } else {
+    for (uint32_t i = tid; i < n1; i += NT)
+      if (M.flag[i]) M.flag[i] = (logf(M.F[i]) >= P.tau) ? 2 : 1;
+  }
+  __syncthreads();
+  // ---- Eq. 22: results in input order
+  const double rho_med = S.rho_med;
+  for (uint32_t i = tid; i < n1; i += NT) {
+    const uint32_t g = M.gidx[i];
+    const uint8_t f = M.flag[i];
+    if (f == 0) write_point<kRec>(A, g, 0, 0.0f, 2);
+    else write_point<kRec>(A, g, f == 2, M.F[i], f == 2 ? 0 : 3);
+    if ((kRec && A.use_dbg) && A.dbg.leaf_rho_med) A.dbg.leaf_rho_med[g] = rho_med;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// persistent kernel
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// 5 CTAs of 128 threads per SM by registers (at most 102 per thread) for K <= 32;
+// the K = 64 lists need more.  kRec: the debug / training outputs are written
+// (a separate instantiation, so that the plain path carries none of their code).
+template <int KMAX, bool kRec>
+__global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 5) k_leaf(const LeafArgs A) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long s_mbar;
+  __shared__ LeafShared S;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lmax = A.lmax;
+  LeafMem Ms;
+  carve<uint16_t>(smem, lmax, KMAX, &Ms, (size_t)lmax * 16);
+  float4 *s_pts = (float4 *)smem;
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint32_t n_leaves = A.ctr->n_leaves;
+  uint32_t phase = 0;
+  for (;;) {
+    if (tid == 0) S.leaf = (ld_volatile(&A.ctr->status) & kStFatal) ? 0xFFFFFFFFu : atomicAdd(&A.ctr->leaf_work, 1u);
+    __syncthreads();
+    const uint32_t wi = S.leaf;  // block-uniform: one thread decided
+    if (wi >= n_leaves) break;
+    const Leaf lf = A.leaves[A.order[wi]];
+    if (lf.count <= lmax) {
+      if (tid == 0) {
+        const uint32_t bytes = lf.count * 16u;
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s_pts);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+            "l"(__cvta_generic_to_global(A.spts + lf.start)), "r"(bytes), "r"(bar)
+            : "memory");
+      }
+      const bool ok = mbar_wait(bar, phase);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(&A.ctr->status, kStTimeout);
+        (void)mbar_wait(bar, phase);  // let the copy in flight land before exiting
+        return;
+      }
+      phase ^= 1u;
+      process_leaf<KMAX, uint16_t, kRec>(A, lf, s_pts, Ms, S);
+    } else {
+      LeafMem Mg;
+      carve<uint32_t>(A.big_scratch + (size_t)lf.start * A.big_bpp, lf.count, KMAX, &Mg, 0);
+      process_leaf<KMAX, uint32_t, kRec>(A, lf, A.spts + lf.start, Mg, S);
+    }
+    __syncthreads();
+  }
+}
+
+template <int KMAX, bool kRec>
+inline int launch_k(const LeafArgs &a, int num_sms, cudaStream_t st) {
+  const size_t smem = leaf_smem_bytes(a.lmax, KMAX);
+  // per call (function attributes are per device, and calls may come from several threads)
+  if (cudaFuncSetAttribute(k_leaf<KMAX, kRec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return -1;
+  cudaFuncSetAttribute(k_leaf<KMAX, kRec>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
+  const int nt = (a.threads == 64) ? 64 : kLeafThreads;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf<KMAX, kRec>, nt, smem) != cudaSuccess ||
+      per_sm < 1)
+    return -1;
+  if (a.ctas_per_sm > 0 && (int)a.ctas_per_sm < per_sm) per_sm = (int)a.ctas_per_sm;
+  k_leaf<KMAX, kRec><<<num_sms * per_sm, nt, smem, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <bool kRec>
+inline int launch_kmax(const LeafArgs &a, int num_sms, cudaStream_t st) {
+  switch (leaf_kmax(a.p.k)) {
+    case 8: return launch_k<8, kRec>(a, num_sms, st);
+    case 16: return launch_k<16, kRec>(a, num_sms, st);
+    case 32: return launch_k<32, kRec>(a, num_sms, st);
+    default: return launch_k<64, kRec>(a, num_sms, st);
+  }
+}
+
+}  // namespace gd

@@ -203,6 +203,34 @@ def test_batch_equals_single_frames(dn, orc):
                              "stage": rs.stage.cpu().numpy()}, ref, P, check_debug=False)
 
 
+def test_async_calls_with_changing_layouts(dn):
+    # back-to-back asynchronous calls on one context, each with a new frame
+    # layout: the pinned tile tables are staged through a ring of slots, so a
+    # call never overwrites a table that an earlier call is still copying
+    import synth
+    from paper_2512_10386_gb300 import Params
+    from paper_2512_10386_gb300 import _native as N
+    P = Params(k=16)
+    clouds = [torch.from_numpy(synth.object_cloud(seed=300 + i, n_surface=n)[0]).cuda()
+              for i, n in enumerate((3000, 9000, 1500, 20000, 6000, 12000, 2500))]
+    ref = [[x.clone() for x in (r.mask, r.score, r.stage)] for r in (dn.run(c, P) for c in clouds)]
+    s = torch.cuda.Stream()
+    outs = [(torch.empty(len(c), dtype=torch.uint8, device="cuda"), torch.empty(len(c), device="cuda"),
+             torch.empty(len(c), dtype=torch.uint8, device="cuda")) for c in clouds]
+    dn.set_sync(False)
+    try:
+        for rep in range(2):
+            for c, (m, sc, st) in zip(clouds, outs):
+                dn.run(c, P, mask=m, score=sc, stage=st, stream=s)
+        s.synchronize()
+        assert dn.status(s) == N.DENOISE_OK
+    finally:
+        dn.set_sync(True)
+    for r, o in zip(ref, outs):
+        for a_, b_ in zip(r, o):
+            assert torch.equal(a_, b_)
+
+
 def test_graph_mode_matches_direct(dn):
     import synth
     xyz, _ = synth.object_cloud(seed=11, n_surface=8000)
