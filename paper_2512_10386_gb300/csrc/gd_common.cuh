@@ -52,6 +52,28 @@ struct Leaf {
 // points from the largest down.
 constexpr int kLeafClasses = 9;
 
+// Programmatic dependent launch: every kernel of a call is launched so that its
+// blocks may be scheduled while the previous kernel drains; pdl_wait() (first
+// access to global memory) blocks until that kernel has completed and its writes
+// are visible, so the stream order of the data is unchanged.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 struct Counters {
   uint32_t status;
   uint32_t n_leaves;

@@ -18,6 +18,7 @@ namespace gd {
 // ---------------------------------------------------------------------------
 __global__ void k_init(FrameInfo *frames, uint32_t nframes, Counters *ctr, uint32_t *digit_hist,
                        uint32_t *lookback, uint32_t n_lookback, int passes) {
+  pdl_wait();
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t stride = gridDim.x * blockDim.x;
   if (tid == 0) {
@@ -49,6 +50,7 @@ __global__ void k_init(FrameInfo *frames, uint32_t nframes, Counters *ctr, uint3
 __global__ void __launch_bounds__(kFrontThreads) k_bbox(const float *__restrict__ xyz,
                                                         FrameInfo *frames, const Tile *__restrict__ tiles,
                                                         Counters *ctr) {
+  pdl_wait();
   const Tile t = tiles[blockIdx.x];
   uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, mx[3] = {0u, 0u, 0u};
   bool bad = false;
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_keys(const float *__restrict_
                                                         uint32_t *__restrict__ hist, int lowbit, int passes,
                                                         const Counters *ctr) {
   __shared__ uint32_t sh[kMaxPasses][256];
+  pdl_wait();
   if (ctr->status & kStFatal) return;
   for (int i = threadIdx.x; i < passes * 256; i += kFrontThreads) (&sh[0][0])[i] = 0;
   __syncthreads();
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(256) k_digit_scan(const uint32_t *__restrict__
                                                     const FrameInfo *__restrict__ frames, int passes,
                                                     const Counters *ctr) {
   __shared__ uint32_t warp_tot[8];
+  pdl_wait();
   if (ctr->status & kStFatal) return;
   const uint32_t f = blockIdx.x / passes, p = blockIdx.x % passes;
   const size_t off = ((size_t)f * kMaxPasses + p) * 256;
@@ -207,6 +211,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
   __shared__ uint32_t s_val[kTilePts];
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_fail;
+  pdl_wait();
   if (ctr->status & kStFatal) return;
   for (int i = threadIdx.x; i < W * 256; i += kFrontThreads) (&s_wcnt[0][0])[i] = 0;
   if (threadIdx.x == 0) {
@@ -354,6 +359,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
 // Without a sort (max_depth 0: one leaf per frame) the points are packed as is.
 __global__ void k_pack(const float *__restrict__ xyz, const Tile *__restrict__ tiles,
                        float4 *__restrict__ pout, const Counters *ctr) {
+  pdl_wait();
   if (ctr->status & kStFatal) return;
   const Tile t = tiles[blockIdx.x];
   for (uint32_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x)
@@ -417,6 +423,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
                                                           Leaf *__restrict__ leaves, Counters *ctr,
                                                           uint32_t cap, int D) {
   extern __shared__ unsigned long long s_win[];
+  pdl_wait();
   if (ctr->status & kStFatal) return;
   // kLeavesSplit blocks share a tile, each taking a contiguous part of it
   const Tile tile = tiles[blockIdx.x / kLeavesSplit];
@@ -534,28 +541,28 @@ int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t
     uint32_t blocks = (work + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > 4096) blocks = 4096;
-    k_init<<<blocks, 256, 0, st>>>(a.frames, a.nframes, a.ctr, a.digit_hist, a.lookback, nlb, passes);
+    launch_pdl(k_init, blocks, 256, 0, st, a.frames, a.nframes, a.ctr, a.digit_hist, a.lookback, nlb, passes);
     ++nl;
   }
-  k_bbox<<<a.ntiles, kFrontThreads, 0, st>>>(a.xyz, a.frames, a.tiles, a.ctr);
-  k_keys<<<a.ntiles, kFrontThreads, 0, st>>>(a.xyz, a.frames, a.tiles, a.keys[0], a.vals[0], a.dbg_key,
+  launch_pdl(k_bbox, a.ntiles, kFrontThreads, 0, st, a.xyz, a.frames, a.tiles, a.ctr);
+  launch_pdl(k_keys, a.ntiles, kFrontThreads, 0, st, a.xyz, a.frames, a.tiles, a.keys[0], a.vals[0], a.dbg_key,
                                              a.digit_hist, lowbit, passes, a.ctr);
   nl += 2;
   if (ev_after_keys) cudaEventRecord(*ev_after_keys, st);
   int cur = 0;
   if (passes > 0) {
-    k_digit_scan<<<a.nframes * passes, 256, 0, st>>>(a.digit_hist, a.digit_base, a.frames, passes, a.ctr);
+    launch_pdl(k_digit_scan, a.nframes * passes, 256, 0, st, a.digit_hist, a.digit_base, a.frames, passes, a.ctr);
     ++nl;
     for (int p = 0; p < passes; ++p) {
       const int shift = lowbit + 8 * p;
       const uint32_t *base = a.digit_base + p * 256;
       uint32_t *lb = a.lookback + (size_t)p * nlb;
       if (p == passes - 1) {
-        k_radix_pass<true><<<a.ntiles, kFrontThreads, 0, st>>>(
+        launch_pdl(k_radix_pass<true>, a.ntiles, kFrontThreads, 0, st,
             a.keys[cur], a.vals[cur], a.keys[cur ^ 1], a.vals[cur ^ 1], a.spts, a.xyz, a.tiles, a.frames,
             base, lb, &a.ctr->tile_work[p], shift, a.ctr);
       } else {
-        k_radix_pass<false><<<a.ntiles, kFrontThreads, 0, st>>>(
+        launch_pdl(k_radix_pass<false>, a.ntiles, kFrontThreads, 0, st,
             a.keys[cur], a.vals[cur], a.keys[cur ^ 1], a.vals[cur ^ 1], a.spts, a.xyz, a.tiles, a.frames,
             base, lb, &a.ctr->tile_work[p], shift, a.ctr);
       }
@@ -563,14 +570,14 @@ int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t
       ++nl;
     }
   } else {
-    k_pack<<<a.ntiles, kFrontThreads, 0, st>>>(a.xyz, a.tiles, a.spts, a.ctr);
+    launch_pdl(k_pack, a.ntiles, kFrontThreads, 0, st, a.xyz, a.tiles, a.spts, a.ctr);
     ++nl;
   }
   if (ev_after_sort) cudaEventRecord(*ev_after_sort, st);
   const size_t win = (a.leaf_capacity <= kLeavesSmemCap)
                         ? sizeof(unsigned long long) * (kLeavesPart + 2 * ((size_t)a.leaf_capacity + 1))
                         : 0;
-  k_leaves<<<a.ntiles * kLeavesSplit, kFrontThreads, win, st>>>(a.keys[cur], a.tiles, a.frames, a.leaves, a.ctr,
+  launch_pdl(k_leaves, a.ntiles * kLeavesSplit, kFrontThreads, win, st,a.keys[cur], a.tiles, a.frames, a.leaves, a.ctr,
                                                                 a.leaf_capacity, a.max_depth);
   ++nl;
   if (launches) *launches += nl;

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_leaf_prep(const float4 *__rest
                                                             const FrameInfo *__restrict__ frames,
                                                             Counters *ctr, float beta, uint32_t lmax) {
   __shared__ float s_ext[kPrepLeaves][3];
+  pdl_wait();
   if (ctr->status & kStFatal) return;
   const uint32_t nl = ctr->n_leaves;
   const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -118,6 +119,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_leaf_prep(const float4 *__rest
 // within a class is arbitrary and does not affect any result.
 __global__ void __launch_bounds__(256) k_leaf_order(const Leaf *__restrict__ leaves, Counters *ctr,
                                                     uint32_t *__restrict__ order, uint32_t lmax) {
+  pdl_wait();
   if (ctr->status & kStFatal) return;
   const uint32_t nl = ctr->n_leaves;
   __shared__ uint32_t s_base[kLeafClasses];
@@ -174,9 +176,9 @@ uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit) {
 }
 
 int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches) {
-  k_leaf_prep<<<num_sms * 4, kPrepThreads, 0, st>>>(a.spts, const_cast<Leaf *>(a.leaves), a.frames, a.ctr, a.p.beta,
+  launch_pdl(k_leaf_prep, num_sms * 4, kPrepThreads, 0, st, a.spts, const_cast<Leaf *>(a.leaves), a.frames, a.ctr, a.p.beta,
                                                    a.lmax);
-  k_leaf_order<<<num_sms * 2, 256, 0, st>>>(a.leaves, a.ctr, a.order, a.lmax);
+  launch_pdl(k_leaf_order, num_sms * 2, 256, 0, st, a.leaves, a.ctr, a.order, a.lmax);
   if (launches) *launches += 2;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -823,6 +823,7 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 5) k_leaf(con
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  pdl_wait();
   const uint32_t n_leaves = A.ctr->n_leaves;
   uint32_t phase = 0;
   for (;;) {
@@ -874,7 +875,7 @@ inline int launch_k(const LeafArgs &a, int num_sms, cudaStream_t st) {
       per_sm < 1)
     return -1;
   if (a.ctas_per_sm > 0 && (int)a.ctas_per_sm < per_sm) per_sm = (int)a.ctas_per_sm;
-  k_leaf<KMAX, kRec><<<num_sms * per_sm, nt, smem, st>>>(a);
+  if (launch_pdl(k_leaf<KMAX, kRec>, num_sms * per_sm, nt, smem, st, a) != cudaSuccess) return -1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
