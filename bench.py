@@ -18,7 +18,7 @@ Extra objects on the line:
                 candidate pair (3 sub + 1 mul + 2 fma of d^2)
   e2e           the same metric through the public call with pinned HOST
                 buffers, copies included
-  cpu_baseline  the FP64 oracle on the machine's host cores, bounded sample
+  cpu_baseline  the FP64 oracle on the host's CPU cores, bounded sample
   batched       64 LiDAR frames (60k-130k points) as one graph-captured batch,
                 against the same frames one call each
 ``--impl reference`` times the FP64 oracle instead (the reference arm).
