@@ -4,6 +4,8 @@
 // Split so the two sets of instantiations compile in parallel.
 #pragma once
 
+#include <type_traits>
+
 #include "gd_common.cuh"
 
 namespace gd {
@@ -569,30 +571,53 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       };
       // every d^2 < theta is a neighbour; the ntie candidates at exactly theta are
       // counted and the position of the last one kept (common case: one tie, the
-      // k_eff-th neighbour itself)
+      // k_eff-th neighbour itself).  The scan goes by chunks of 32 candidates: two
+      // bit masks (d^2 < theta, d^2 <= theta) per chunk, then the neighbours of the
+      // chunk are emitted from the first mask in position order.
       uint32_t a = 0, ntie = 0, tp = 0;
-      for (uint32_t j = 0; j < n1; j += 4) {
-        float4 cv[4];
-        float dv[4];
+      auto chunk = [&](uint32_t c0, auto full_chunk) {
+        constexpr bool kFull = decltype(full_chunk)::value;
+        uint32_t lt = 0, le = 0;
+#pragma unroll 2
+        for (uint32_t st = 0; st < 8; ++st) {
+          float dv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          cv[u] = M.p1[(j + u < n1) ? j + u : j];
-          dv[u] = sqdist(me, cv[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const uint32_t ju = j + u;
-          if (ju < n1 && ju != qq) {
-            if (dv[u] < theta) {
-              if (act && a < keff) emit(a, ju, __float_as_uint(cv[u].w), dv[u]);
-              ++a;
-            } else if (dv[u] == theta) {
-              ++ntie;
-              tp = ju;
-            }
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t ju = c0 + st * 4 + u;
+            dv[u] = sqdist(me, M.p1[(kFull || ju < n1) ? ju : c0]);
           }
+          uint32_t nl = 0, ne = 0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            nl |= (dv[u] < theta) ? (1u << u) : 0u;
+            ne |= (dv[u] <= theta) ? (1u << u) : 0u;
+          }
+          lt |= nl << (st * 4);
+          le |= ne << (st * 4);
         }
-      }
+        // the query itself, and positions past n1 in the last chunk, are no candidates
+        uint32_t keep = (qq - c0 < 32u) ? ~(1u << (qq - c0)) : 0xFFFFFFFFu;
+        if (!kFull) keep &= (1u << (n1 - c0)) - 1u;
+        lt &= keep;
+        le &= keep;
+        const uint32_t tie = le & ~lt;
+        if (tie) {
+          ntie += __popc(tie);
+          tp = c0 + 31u - __clz(tie);
+        }
+        while (lt) {
+          const uint32_t ju = c0 + (uint32_t)(__ffs(lt) - 1);
+          lt &= lt - 1u;
+          if (act && a < keff) {
+            const float4 cj = M.p1[ju];
+            emit(a, ju, __float_as_uint(cj.w), sqdist(me, cj));
+          }
+          ++a;
+        }
+      };
+      uint32_t c0 = 0;
+      for (; c0 + 32u <= n1; c0 += 32u) chunk(c0, std::true_type{});
+      if (c0 < n1) chunk(c0, std::false_type{});
       if (act && a != below) atomicOr(&A.ctr->status, kStInternal);  // the two phases must agree
       // ties: with exactly ties_needed of them all are taken, otherwise the
       // ties_needed smallest input indices (rare: exact lattices, duplicates)
