@@ -6,6 +6,8 @@
 
 #include <type_traits>
 
+#include <type_traits>
+
 #include "gd_common.cuh"
 
 namespace gd {
@@ -15,6 +17,10 @@ constexpr int kLeafWarps = kLeafThreads / 32;
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned long long kInvalid = ~0ull - 1ull;
 constexpr uint32_t kPend = 8;  // parking slots per lane: a warp merges before any lane could overflow
+// P_1 is followed by kPad NaN points: the kNN scans run to the next multiple of 4
+// (phase A) or of 32 (phase B) without a bounds test, since a NaN distance is
+// neither below nor equal to any threshold.
+constexpr uint32_t kPad = 32;
 // the sort buffer also holds the parked candidates during the kNN
 constexpr size_t kPendBytes = (size_t)kPend * kLeafThreads * sizeof(float);
 
@@ -27,7 +33,7 @@ __host__ __device__ __forceinline__ uint32_t pow2ceil(uint32_t x) {
 
 // Per-leaf working arrays: shared memory (small leaves) or global spill (large).
 struct LeafMem {
-  float4 *p1;                // [cap] P_1 points; w = input index (bits)
+  float4 *p1;                // [cap + kPad] P_1 points (w = input index bits), then NaN sentinels
   unsigned long long *hkey;  // [hcap] voxel hash keys
   uint32_t *hcnt;            // [hcap] voxel occupancy
   unsigned long long *sbuf;  // [scap] sort buffer
@@ -77,7 +83,7 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
   size_t o = off;
   auto take = [&](size_t bytes) { size_t r = o; o = al16(o + bytes); return r; };
   const size_t sbytes = (size_t)scap * 8 > kPendBytes ? (size_t)scap * 8 : kPendBytes;
-  const size_t p1 = take((size_t)cap * 16), sb = take(sbytes);
+  const size_t p1 = take((size_t)(cap + kPad) * 16), sb = take(sbytes);
   const size_t r2 = take((size_t)cap * 4), wa = take((size_t)cap * 4), wc = take((size_t)cap * 4);
   const size_t F = take((size_t)cap * 4), gi = take((size_t)cap * 4);
   const size_t fl = take((size_t)cap);
@@ -445,6 +451,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       uint32_t t = 0;
       for (uint32_t ww = 0; ww < NW; ++ww) t += S.wsum[ww];
       S.run += t;
+      if (base + NT >= nt)  // last round: the sentinels after P_1
+        for (uint32_t u = 0; u < kPad; ++u) M.p1[S.run + u] = make_float4(NAN, NAN, NAN, 0.0f);
     }
     __syncthreads();
   }
@@ -511,33 +519,29 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         L[sl] = v;
       }
       regsort_f<KMAX>(L);
+      // steps of 4 candidates: [j0, n1 rounded up to 4) (the tail reads sentinels),
+      // then [0, j0); the last step also merges what is still parked
       uint32_t np = 0;
-      for (uint32_t pass = 0; pass < 2; ++pass) {
-        const uint32_t jb = pass == 0 ? j0 : 0u, je = pass == 0 ? n1 : j0;
-        for (uint32_t j = jb; j < je; j += 4) {
-          uint32_t jj[4];
-          float dd[4];
+      const uint32_t s0 = (n1 - j0 + 3u) >> 2, ns = s0 + (j0 >> 2);
+      const uint32_t wlen = we - ws;  // candidate j is a seed (or the query) iff j - ws <= wlen, unsigned
+      for (uint32_t sI = 0; sI < ns; ++sI) {
+        const uint32_t j = (sI < s0) ? j0 + 4u * sI : 4u * (sI - s0);
+        float dd[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const bool ok = j + u < je;
-            jj[u] = ok ? j + u : j;
-            dd[u] = ok ? sqdist(me, M.p1[jj[u]]) : INFINITY;
-          }
-          const float thr = L[KMAX - 1];
+        for (int u = 0; u < 4; ++u) dd[u] = sqdist(me, M.p1[j + u]);
+        const float thr = L[KMAX - 1];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (dd[u] < thr && (jj[u] < ws || jj[u] > we)) {
-              pend[np * kLeafThreads + tid] = dd[u];
-              ++np;
-            }
-          }
-          if (__any_sync(0xFFFFFFFFu, np + 4 > kPend)) {
-            merge_pending<KMAX>(L, pend, np, tid);
-            np = 0;
+        for (int u = 0; u < 4; ++u) {
+          if (dd[u] < thr && j + u - ws > wlen) {
+            pend[np * kLeafThreads + tid] = dd[u];
+            ++np;
           }
         }
+        if (__any_sync(0xFFFFFFFFu, np + 4 > kPend || sI + 1 == ns)) {
+          merge_pending<KMAX>(L, pend, np, tid);
+          np = 0;
+        }
       }
-      merge_pending<KMAX>(L, pend, np, tid);
       const float theta = L[KMAX - 1];
       uint32_t below = 0;
 #pragma unroll
@@ -575,17 +579,13 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       // bit masks (d^2 < theta, d^2 <= theta) per chunk, then the neighbours of the
       // chunk are emitted from the first mask in position order.
       uint32_t a = 0, ntie = 0, tp = 0;
-      auto chunk = [&](uint32_t c0, auto full_chunk) {
-        constexpr bool kFull = decltype(full_chunk)::value;
+      for (uint32_t c0 = 0; c0 < n1; c0 += 32u) {
         uint32_t lt = 0, le = 0;
 #pragma unroll 2
         for (uint32_t st = 0; st < 8; ++st) {
           float dv[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const uint32_t ju = c0 + st * 4 + u;
-            dv[u] = sqdist(me, M.p1[(kFull || ju < n1) ? ju : c0]);
-          }
+          for (int u = 0; u < 4; ++u) dv[u] = sqdist(me, M.p1[c0 + st * 4 + u]);
           uint32_t nl = 0, ne = 0;
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -595,9 +595,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           lt |= nl << (st * 4);
           le |= ne << (st * 4);
         }
-        // the query itself, and positions past n1 in the last chunk, are no candidates
-        uint32_t keep = (qq - c0 < 32u) ? ~(1u << (qq - c0)) : 0xFFFFFFFFu;
-        if (!kFull) keep &= (1u << (n1 - c0)) - 1u;
+        // the query itself is no candidate (positions past n1 are sentinels: no bits)
+        const uint32_t keep = (qq - c0 < 32u) ? ~(1u << (qq - c0)) : 0xFFFFFFFFu;
         lt &= keep;
         le &= keep;
         const uint32_t tie = le & ~lt;
@@ -614,10 +613,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           }
           ++a;
         }
-      };
-      uint32_t c0 = 0;
-      for (; c0 + 32u <= n1; c0 += 32u) chunk(c0, std::true_type{});
-      if (c0 < n1) chunk(c0, std::false_type{});
+      }
       if (act && a != below) atomicOr(&A.ctr->status, kStInternal);  // the two phases must agree
       // ties: with exactly ties_needed of them all are taken, otherwise the
       // ties_needed smallest input indices (rare: exact lattices, duplicates)
