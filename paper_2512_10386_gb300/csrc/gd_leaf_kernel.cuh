@@ -344,6 +344,30 @@ __device__ __forceinline__ void merge_pending(float (&L)[KMAX], const float *pen
   }
 }
 
+// Lref of the score (Eq. 16-17), from the lower-middle r^2 (ra) and upper-middle
+// r^2 (rb) of P_2's m points.  Once per leaf by one thread: kept out of line.
+static __device__ __noinline__ float leaf_lref(float ra, float rb, uint32_t m, uint32_t keff, float eps_rho) {
+  // log2(rho(ra) / rho_med): 0 for odd m, 1 - log2(1 + (ra / rb)^1.5) for even m
+  float lr = 0.0f;
+  if (!(m & 1u)) {
+    const float t = __fdiv_rn(ra, rb);
+    lr = __fsub_rn(1.0f, log2f(__fadd_rn(1.0f, __fmul_rn(t, sqrtf(t)))));
+  }
+  // log2(rho_med) = log2(rho(ra)) - lr, with log2(rho(ra)) = log2(k_eff) - log2(4/3 pi) - 1.5 log2(ra)
+  const float l_rho_a =
+      __fsub_rn(__fsub_rn(log2f((float)keff), 2.0665336287511624f), __fmul_rn(1.5f, log2f(ra)));
+  const float l_med = __fsub_rn(l_rho_a, lr);
+  float corr = 0.0f;
+  if (eps_rho > 0.0f) {
+    const float lx = __fsub_rn(log2f(eps_rho), __fmul_rn(2.0f, l_med));  // log2(eps_rho / rho_med^2)
+    corr = (lx > 100.0f) ? __fmul_rn(0.5f, lx) : __fmul_rn(0.5f, log2f(__fadd_rn(1.0f, exp2f(lx))));
+  }
+  return __fsub_rn(lr, corr);
+}
+
+// (d^2)^(gamma/2) for gamma != 2 (the score's common case gamma = 2 needs none): out of line
+static __device__ __noinline__ float pow_half_gamma(float d2, float hg) { return exp2f(__fmul_rn(hg, log2f(d2))); }
+
 template <bool kRec>
 __device__ __forceinline__ void write_point(const LeafArgs &A, uint32_t g, uint8_t mk, float sc, uint8_t st) {
   if (g >= A.n) {  // cannot happen with a consistent sort; never write out of bounds
@@ -681,27 +705,10 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   // log2(rho_med) - 0.5 log2(1 + eps_rho / rho_med^2).  Every term is a log2 of a
   // ratio near 1 (or the eps correction), evaluated in FP32 without overflow.
   if (tid == 0) {
-    const uint32_t mid = (m - 1) / 2;
-    const float ra = __uint_as_float(vbuf[mid]);
-    // log2(rho(ra) / rho_med): 0 for odd m, 1 - log2(1 + (ra / rb)^1.5) for even m
-    float lr = 0.0f;
-    float rb = ra;
-    if (!(m & 1u)) {
-      rb = __uint_as_float(vbuf[m / 2]);
-      const float t = __fdiv_rn(ra, rb);
-      lr = __fsub_rn(1.0f, log2f(__fadd_rn(1.0f, __fmul_rn(t, sqrtf(t)))));
-    }
-    // log2(rho_med) = log2(rho(ra)) - lr, with log2(rho(ra)) = log2(k_eff) - log2(4/3 pi) - 1.5 log2(ra)
-    const float l_rho_a =
-        __fsub_rn(__fsub_rn(log2f((float)keff), 2.0665336287511624f), __fmul_rn(1.5f, log2f(ra)));
-    const float l_med = __fsub_rn(l_rho_a, lr);
-    float corr = 0.0f;
-    if (P.eps_rho > 0.0f) {
-      const float lx = __fsub_rn(log2f(P.eps_rho), __fmul_rn(2.0f, l_med));  // log2(eps_rho / rho_med^2)
-      corr = (lx > 100.0f) ? __fmul_rn(0.5f, lx) : __fmul_rn(0.5f, log2f(__fadd_rn(1.0f, exp2f(lx))));
-    }
+    const float ra = __uint_as_float(vbuf[(m - 1) / 2]);
+    const float rb = (m & 1u) ? ra : __uint_as_float(vbuf[m / 2]);
     S.r2ref = ra;
-    S.Lref = __fsub_rn(lr, corr);
+    S.Lref = leaf_lref(ra, rb, m, keff, P.eps_rho);
     S.keep_n = (uint32_t)ceil((double)P.lambda * (double)m);
     if (S.keep_n > m) S.keep_n = m;
     atomicAdd(&A.ctr->n_p2, (unsigned long long)m);
@@ -761,16 +768,15 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         }
         const float d2 = sqdist(me, M.p1[j]);
         const float wt = ex2_hw(__fmaf_rn(-d2, ci, __fadd_rn(ai, M.wa[j])));  // w_den * w_dis (Eq. 17, 19)
-        const float D = g2 ? d2 : exp2f(__fmul_rn(hg, log2f(d2)));          // (d^2)^(gamma/2)
+        const float D = g2 ? d2 : pow_half_gamma(d2, hg);                    // (d^2)^(gamma/2)
         return __fmul_rn(wt, rcp_hw(__fadd_rn(D, ek)));                    // kernel of Eq. 20
       };
-      uint32_t t = 0;
-      for (; t + 1 < keff; t += 2) {
-        const float e0 = term(t), e1 = term(t + 1);
-        F0 = __fadd_rn(F0, e0);
-        F1 = __fadd_rn(F1, e1);
+#pragma unroll 1
+      for (uint32_t t = 0; t < keff; ++t) {  // one copy of the term's code
+        const float e = term(t);
+        if (t & 1u) F1 = __fadd_rn(F1, e);
+        else F0 = __fadd_rn(F0, e);
       }
-      if (t < keff) F0 = __fadd_rn(F0, term(t));
       M.F[i] = __fadd_rn(F0, F1);
     }
   }
