@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) k_leaf_order(const Leaf *__restrict__ lea
 int leaf_kmax(uint32_t k) { return k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64; }
 
 size_t leaf_smem_bytes(uint32_t lmax, int kmax) {
-  return carve<uint16_t>(nullptr, lmax, kmax, nullptr, (size_t)lmax * 16);
+  return carve<uint16_t>(nullptr, lmax, kmax, nullptr);
 }
 
 uint32_t leaf_big_bpp(int kmax) {
@@ -160,7 +160,7 @@ uint32_t leaf_big_bpp(int kmax) {
   if (kmax <= 64 && cached[kmax]) return cached[kmax];
   size_t worst = 0;
   for (uint32_t cap = 65; cap <= 65536; ++cap) {
-    const size_t b = carve<uint32_t>(nullptr, cap, kmax, nullptr, 0);
+    const size_t b = carve<uint32_t>(nullptr, cap, kmax, nullptr);
     const size_t per = (b + cap - 1) / cap;
     if (per > worst) worst = per;
   }

@@ -37,8 +37,8 @@ struct LeafMem {
   unsigned long long *hkey;  // [hcap] voxel hash keys
   uint32_t *hcnt;            // [hcap] voxel occupancy
   unsigned long long *sbuf;  // [scap] sort buffer
-  float *r2, *wa, *wc, *F;   // [cap] per P_1 position
-  uint32_t *gidx;            // [cap] global input index per P_1 position
+  float *r2, *wa;            // [cap] per P_1 position: r_K^2, (alpha/2) ell
+  float *F;                  // [cap] score; shares r2's storage (F_i is written after r2_i's last read)
   uint8_t *flag;             // [cap] 0 removed by density gate, 1 scored, 2 kept
   void *nbr;                 // neighbour positions: see nb_bits (shared memory) or [KMAX][cap] u32 (global)
   uint32_t hcap, scap, cap;
@@ -47,7 +47,7 @@ struct LeafMem {
 // Neighbour table of the shared-memory path: query q owns nb_words(cap, kmax)
 // consecutive 32-bit words holding its neighbour positions as nb_bits(cap)-bit
 // fields, rank t at bit t * nb_bits (a 512-point leaf needs 9 bits, not 16).
-// The packing keeps a 512-point, K = 32 CTA under 45 KB: 5 CTAs per SM.
+// The packing keeps a 512-point, K = 32 CTA at 35 KB: 6 CTAs per SM.
 __host__ __device__ __forceinline__ uint32_t nb_bits(uint32_t cap) {
   uint32_t b = 1;
   while ((1u << b) < cap) ++b;
@@ -58,23 +58,21 @@ __host__ __device__ __forceinline__ uint32_t nb_words(uint32_t cap, int kmax) {
   return (((uint32_t)kmax * nb_bits(cap) + 31u) / 32u) | 1u;
 }
 
-// Layout of the per-leaf arrays.  `alias_head` bytes at the start (the TMA
-// landing zone of the leaf's raw points) are shared with the hash table and
-// the neighbour table, whose lifetimes do not overlap with it.
+// Layout of the per-leaf arrays.  Region A holds the voxel hash table, later
+// (the lifetimes do not overlap) the neighbour table.  The raw points of a
+// shared-memory leaf land in p1 and are compacted in place into P_1.
 template <typename IdxT>
-__host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t cap, int kmax, LeafMem *m,
-                                                 size_t head_bytes) {
+__host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t cap, int kmax, LeafMem *m) {
   const uint32_t hcap = pow2ceil(2 * cap), scap = pow2ceil(cap);
-  // region A: max(raw points + hash table, neighbour table)
-  const size_t hash_off = al16(head_bytes);
-  const size_t hash_end = hash_off + al16((size_t)hcap * 8) + al16((size_t)hcap * 4);
+  // region A: max(hash table, neighbour table)
+  const size_t hash_end = al16((size_t)hcap * 8) + al16((size_t)hcap * 4);
   const size_t nbr_bytes = (sizeof(IdxT) == 2) ? al16((size_t)cap * nb_words(cap, kmax) * 4)
                                                : al16((size_t)cap * kmax * sizeof(IdxT));
   size_t off = hash_end > nbr_bytes ? hash_end : nbr_bytes;
   off = al16(off);
   if (m) {
-    m->hkey = (unsigned long long *)(base + hash_off);
-    m->hcnt = (uint32_t *)(base + hash_off + al16((size_t)hcap * 8));
+    m->hkey = (unsigned long long *)base;
+    m->hcnt = (uint32_t *)(base + al16((size_t)hcap * 8));
     m->nbr = (void *)base;
     m->hcap = hcap;
     m->scap = scap;
@@ -84,17 +82,14 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
   auto take = [&](size_t bytes) { size_t r = o; o = al16(o + bytes); return r; };
   const size_t sbytes = (size_t)scap * 8 > kPendBytes ? (size_t)scap * 8 : kPendBytes;
   const size_t p1 = take((size_t)(cap + kPad) * 16), sb = take(sbytes);
-  const size_t r2 = take((size_t)cap * 4), wa = take((size_t)cap * 4), wc = take((size_t)cap * 4);
-  const size_t F = take((size_t)cap * 4), gi = take((size_t)cap * 4);
+  const size_t r2 = take((size_t)cap * 4), wa = take((size_t)cap * 4);
   const size_t fl = take((size_t)cap);
   if (m) {
     m->p1 = (float4 *)(base + p1);
     m->sbuf = (unsigned long long *)(base + sb);
     m->r2 = (float *)(base + r2);
     m->wa = (float *)(base + wa);
-    m->wc = (float *)(base + wc);
-    m->F = (float *)(base + F);
-    m->gidx = (uint32_t *)(base + gi);
+    m->F = m->r2;
     m->flag = (uint8_t *)(base + fl);
   }
   return o;
@@ -467,8 +462,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     for (uint32_t ww = 0; ww < w; ++ww) off += S.wsum[ww];
     if (in1) {
       const uint32_t pos = off + __popc(bal & lt);
-      M.p1[pos] = p;
-      M.gidx[pos] = g;
+      M.p1[pos] = p;  // in place for a shared-memory leaf: pos <= i, and this round's reads are done
     }
     __syncthreads();
     if (tid == 0) {
@@ -482,7 +476,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   }
   const uint32_t n1 = S.run;
   if (n1 <= 1) {  // no neighbour exists: the density gate cannot keep it
-    for (uint32_t i = tid; i < n1; i += NT) write_point<kRec>(A, M.gidx[i], 0, 0.0f, 2);
+    for (uint32_t i = tid; i < n1; i += NT) write_point<kRec>(A, __float_as_uint(M.p1[i].w), 0, 0.0f, 2);
     return;
   }
   const uint32_t keff = (P.k < n1 - 1) ? P.k : n1 - 1;
@@ -571,7 +565,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
 #pragma unroll
       for (int sl = 0; sl < KMAX; ++sl) below += (L[sl] >= 0.0f && L[sl] < theta) ? 1u : 0u;
       const uint32_t ties_needed = keff - below;  // >= 1: theta itself is a candidate
-      const uint32_t gq = M.gidx[qq];
+      const uint32_t gq = __float_as_uint(me.w);
       // Record neighbour t of this query (position npos, input index g, distance d2).
       // Ranks come in order t = 0, 1, ...: the packed table is filled through a
       // bit buffer, one word store per 32 bits.
@@ -722,16 +716,16 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     }
   }
   __syncthreads();
+  // distance weight exponent: w_dis = 2^(-d^2 c_i) with c_i = c2 / r2_i, c2 = log2(e) / (2 sigma^2)
+  const float c2 = __fdiv_rn(1.4426950408889634f, __fmul_rn(__fmul_rn(2.0f, P.sigma), P.sigma));
   {
     const float r2ref = S.r2ref, Lref = S.Lref;
     const float half_alpha = __fmul_rn(0.5f, P.alpha);
-    const float c2 = __fdiv_rn(1.4426950408889634f, __fmul_rn(__fmul_rn(2.0f, P.sigma), P.sigma));
     for (uint32_t i = tid; i < n1; i += NT) {
       const float r2 = M.r2[i];
       const float ell = __fsub_rn(Lref, __fmul_rn(1.5f, log2f(__fdiv_rn(r2, r2ref))));  // log2(rho_i / sqrt(rho_med^2 + eps))
       M.wa[i] = __fmul_rn(half_alpha, ell);
-      M.wc[i] = __fdiv_rn(c2, r2);
-      if ((kRec && A.use_train)) A.train.ell[M.gidx[i]] = ell;
+      if ((kRec && A.use_train)) A.train.ell[__float_as_uint(M.p1[i].w)] = ell;
     }
   }
   __syncthreads();
@@ -745,7 +739,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     for (uint32_t i = tid; i < n1; i += NT) {
       if (!M.flag[i]) continue;
       const float4 me = M.p1[i];
-      const float ai = M.wa[i], ci = M.wc[i];
+      const float ai = M.wa[i], ci = __fdiv_rn(c2, M.r2[i]);  // r2_i's last read: F_i takes its place
       // two neighbours per step into two partial sums (independent chains),
       // F = even-rank terms + odd-rank terms
       float F0 = 0.0f, F1 = 0.0f;
@@ -788,7 +782,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     for (uint32_t i = tid; i < sn; i += NT) {
       unsigned long long key = kEmpty;
       if (i < n1 && M.flag[i])
-        key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | M.gidx[i];
+        key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | __float_as_uint(M.p1[i].w);
       M.sbuf[i] = key;
     }
     __syncthreads();
@@ -796,7 +790,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     const unsigned long long cut = M.sbuf[S.keep_n - 1];
     for (uint32_t i = tid; i < n1; i += NT) {
       if (!M.flag[i]) continue;
-      const unsigned long long key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | M.gidx[i];
+      const unsigned long long key =
+          ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | __float_as_uint(M.p1[i].w);
       M.flag[i] = (key <= cut) ? 2 : 1;
     }
   } else {
@@ -807,7 +802,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   // ---- Eq. 22: results in input order
   const double rho_med = S.rho_med;
   for (uint32_t i = tid; i < n1; i += NT) {
-    const uint32_t g = M.gidx[i];
+    const uint32_t g = __float_as_uint(M.p1[i].w);
     const uint8_t f = M.flag[i];
     if (f == 0) write_point<kRec>(A, g, 0, 0.0f, 2);
     else write_point<kRec>(A, g, f == 2, M.F[i], f == 2 ? 0 : 3);
@@ -831,19 +826,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
   return false;
 }
 
-// 5 CTAs of 128 threads per SM by registers (at most 102 per thread) for K <= 32;
+// 6 CTAs of 128 threads per SM by registers (at most 85 per thread) for K <= 32
+// (a 512-point, K = 32 leaf takes 35 KB of shared memory, so 6 fit there too);
 // the K = 64 lists need more.  kRec: the debug / training outputs are written
 // (a separate instantiation, so that the plain path carries none of their code).
 template <int KMAX, bool kRec>
-__global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 5) k_leaf(const LeafArgs A) {
+__global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 6) k_leaf(const LeafArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long s_mbar;
   __shared__ LeafShared S;
   const uint32_t tid = threadIdx.x;
   const uint32_t lmax = A.lmax;
   LeafMem Ms;
-  carve<uint16_t>(smem, lmax, KMAX, &Ms, (size_t)lmax * 16);
-  float4 *s_pts = (float4 *)smem;
+  carve<uint16_t>(smem, lmax, KMAX, &Ms);
+  float4 *const s_pts = Ms.p1;  // the raw points land in p1 (compacted in place)
   const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -880,7 +876,7 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 5) k_leaf(con
       process_leaf<KMAX, uint16_t, kRec>(A, lf, s_pts, Ms, S);
     } else {
       LeafMem Mg;
-      carve<uint32_t>(A.big_scratch + (size_t)lf.start * A.big_bpp, lf.count, KMAX, &Mg, 0);
+      carve<uint32_t>(A.big_scratch + (size_t)lf.start * A.big_bpp, lf.count, KMAX, &Mg);
       process_leaf<KMAX, uint32_t, kRec>(A, lf, A.spts + lf.start, Mg, S);
     }
     __syncthreads();
