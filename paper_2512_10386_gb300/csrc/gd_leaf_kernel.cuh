@@ -16,7 +16,10 @@ constexpr int kLeafThreads = 128;
 constexpr int kLeafWarps = kLeafThreads / 32;
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned long long kInvalid = ~0ull - 1ull;
-constexpr uint32_t kPend = 8;  // parking slots per lane: a warp merges before any lane could overflow
+constexpr uint32_t kPend = 12;  // parking slots per lane (at most): a warp merges before any lane could overflow
+// slots used for a list of KMAX values (the merge keeps the KMAX smallest of list and slots)
+template <int KMAX>
+__host__ __device__ constexpr uint32_t pend_slots() { return KMAX >= 16 ? 12u : 8u; }
 // P_1 is followed by kPad NaN points: the kNN scans run to the next multiple of 4
 // (phase A) or of 32 (phase B) without a bounds test, since a NaN distance is
 // neither below nor equal to any threshold.
@@ -80,9 +83,12 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
   }
   size_t o = off;
   auto take = [&](size_t bytes) { size_t r = o; o = al16(o + bytes); return r; };
-  const size_t sbytes = (size_t)scap * 8 > kPendBytes ? (size_t)scap * 8 : kPendBytes;
-  const size_t p1 = take((size_t)(cap + kPad) * 16), sb = take(sbytes);
-  const size_t r2 = take((size_t)cap * 4), wa = take((size_t)cap * 4);
+  // the parked kNN candidates use the sort buffer and wa (idle during the kNN), adjacent here
+  const size_t wa_bytes = al16((size_t)cap * 4);
+  const size_t sneed = kPendBytes > wa_bytes ? kPendBytes - wa_bytes : 0;
+  const size_t sbytes = (size_t)scap * 8 > sneed ? (size_t)scap * 8 : sneed;
+  const size_t p1 = take((size_t)(cap + kPad) * 16), r2 = take((size_t)cap * 4);
+  const size_t sb = take(sbytes), wa = take((size_t)cap * 4);
   const size_t fl = take((size_t)cap);
   if (m) {
     m->p1 = (float4 *)(base + p1);
@@ -340,12 +346,13 @@ __device__ __forceinline__ void regsort_f(float (&L)[N]) {
 // order with a half-cleaner cascade.
 template <int KMAX>
 __device__ __forceinline__ void merge_pending(float (&L)[KMAX], const float *pend, uint32_t np, uint32_t tid) {
-  float B[kPend];
+  constexpr int NP = (int)pend_slots<KMAX>();
+  float B[NP];
 #pragma unroll
-  for (int i = 0; i < (int)kPend; ++i) B[i] = ((uint32_t)i < np) ? pend[i * kLeafThreads + tid] : INFINITY;
-  regsort_f<kPend>(B);
+  for (int i = 0; i < NP; ++i) B[i] = ((uint32_t)i < np) ? pend[i * kLeafThreads + tid] : INFINITY;
+  regsort_f<NP>(B);
 #pragma unroll
-  for (int i = 0; i < (int)kPend; ++i) L[KMAX - kPend + i] = fminf(L[KMAX - kPend + i], B[kPend - 1 - i]);
+  for (int i = 0; i < NP; ++i) L[KMAX - NP + i] = fminf(L[KMAX - NP + i], B[NP - 1 - i]);
 #pragma unroll
   for (int j = KMAX / 2; j > 0; j >>= 1) {
 #pragma unroll
@@ -575,7 +582,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
             ++np;
           }
         }
-        if (__any_sync(0xFFFFFFFFu, np + 4 > kPend || sI + 1 == ns)) {
+        if (__any_sync(0xFFFFFFFFu, np + 4 > pend_slots<KMAX>() || sI + 1 == ns)) {
           merge_pending<KMAX>(L, pend, np, tid);
           np = 0;
         }
