@@ -625,23 +625,28 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       // chunk are emitted from the first mask in position order.
       uint32_t a = 0, ntie = 0, tp = 0;
       for (uint32_t c0 = 0; c0 < n1; c0 += 32u) {
-        uint32_t lt = 0, le = 0;
+        // The comparisons go through the FMA pipe: for IEEE subtraction (no flush to
+        // zero) x - y is negative exactly when x < y, so the sign bit of d^2 - theta is
+        // (d^2 < theta) and that of theta - d^2 is !(d^2 <= theta) (NaN gives sign 0).
+        // A funnel shift appends each sign bit: the chunk's first candidate ends in bit 31.
+        uint32_t lt = 0, gt = 0;
 #pragma unroll 2
         for (uint32_t st = 0; st < 8; ++st) {
           float dv[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) dv[u] = sqdist(me, M.p1[c0 + st * 4 + u]);
-          uint32_t nl = 0, ne = 0;
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            nl |= (dv[u] < theta) ? (1u << u) : 0u;
-            ne |= (dv[u] <= theta) ? (1u << u) : 0u;
+            lt = __funnelshift_l(__float_as_uint(__fsub_rn(dv[u], theta)), lt, 1);
+            gt = __funnelshift_l(__float_as_uint(__fsub_rn(theta, dv[u])), gt, 1);
           }
-          lt |= nl << (st * 4);
-          le |= ne << (st * 4);
         }
-        // the query itself is no candidate (positions past n1 are sentinels: no bits)
-        const uint32_t keep = (qq - c0 < 32u) ? ~(1u << (qq - c0)) : 0xFFFFFFFFu;
+        lt = __brev(lt);
+        uint32_t le = __brev(~gt);
+        // the query itself is no candidate; positions past n1 (NaN sentinels) are
+        // outside d^2 < theta already and are masked out of d^2 <= theta
+        uint32_t keep = (qq - c0 < 32u) ? ~(1u << (qq - c0)) : 0xFFFFFFFFu;
+        if (n1 - c0 < 32u) keep &= (1u << (n1 - c0)) - 1u;
         lt &= keep;
         le &= keep;
         const uint32_t tie = le & ~lt;
