@@ -24,6 +24,7 @@ __host__ __device__ constexpr uint32_t pend_slots() { return KMAX >= 16 ? 12u : 
 // (phase A) or of 32 (phase B) without a bounds test, since a NaN distance is
 // neither below nor equal to any threshold.
 constexpr uint32_t kPad = 32;
+constexpr uint32_t kPadFront = 4;  // NaN points before P_1 too (a backward scan may start below 0)
 // the sort buffer also holds the parked candidates during the kNN
 constexpr size_t kPendBytes = (size_t)kPend * kLeafThreads * sizeof(float);
 
@@ -36,7 +37,7 @@ __host__ __device__ __forceinline__ uint32_t pow2ceil(uint32_t x) {
 
 // Per-leaf working arrays: shared memory (small leaves) or global spill (large).
 struct LeafMem {
-  float4 *p1;                // [cap + kPad] P_1 points (w = input index bits), then NaN sentinels
+  float4 *p1;                // [cap + kPad] P_1 points (w = input index bits), then NaN sentinels; kPadFront before
   unsigned long long *hkey;  // [hcap] voxel hash keys
   uint32_t *hcnt;            // [hcap] voxel occupancy
   unsigned long long *sbuf;  // [scap] sort buffer
@@ -87,7 +88,7 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
   const size_t wa_bytes = al16((size_t)cap * 4);
   const size_t sneed = kPendBytes > wa_bytes ? kPendBytes - wa_bytes : 0;
   const size_t sbytes = (size_t)scap * 8 > sneed ? (size_t)scap * 8 : sneed;
-  const size_t p1 = take((size_t)(cap + kPad) * 16), r2 = take((size_t)cap * 4);
+  const size_t p1 = take((size_t)(kPadFront + cap + kPad) * 16) + kPadFront * 16, r2 = take((size_t)cap * 4);
   const size_t sb = take(sbytes), wa = take((size_t)cap * 4);
   const size_t fl = take((size_t)cap);
   if (m) {
@@ -498,6 +499,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       S.run += t;
       if (base + NT >= nt)  // last round: the sentinels after P_1
         for (uint32_t u = 0; u < kPad; ++u) M.p1[S.run + u] = make_float4(NAN, NAN, NAN, 0.0f);
+      if (base + NT >= nt)
+        for (int u = 1; u <= (int)kPadFront; ++u) M.p1[-u] = make_float4(NAN, NAN, NAN, 0.0f);
     }
     __syncthreads();
   }
@@ -547,8 +550,12 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       const uint32_t qq = act ? q : n1 - 1;          // idle lanes shadow a real query, results discarded
       const float4 me = M.p1[qq];
       const uint32_t j0 = qb + w * 32;               // < n1: lane 0 of a busy warp is busy
+      // Seed window [ws, we] (k_eff + 1 positions holding the query): with k_eff >= 32
+      // one window for the whole warp (it holds the warp's 32 queries), so that the
+      // scan needs no per-lane window test; otherwise centred on the lane's query.
+      const bool uni = keff >= 32u;
       const uint32_t half = keff / 2;
-      uint32_t ws = (qq > half) ? qq - half : 0u;
+      uint32_t ws = uni ? j0 : ((qq > half) ? qq - half : 0u);
       if (ws > n1 - 1 - keff) ws = n1 - 1 - keff;
       const uint32_t we = ws + keff;
       float L[KMAX];
@@ -564,27 +571,51 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         L[sl] = v;
       }
       regsort_f<KMAX>(L);
-      // steps of 4 candidates: [j0, n1 rounded up to 4) (the tail reads sentinels),
-      // then [0, j0); the last step also merges what is still parked
       uint32_t np = 0;
-      const uint32_t s0 = (n1 - j0 + 3u) >> 2, ns = s0 + (j0 >> 2);
-      const uint32_t wlen = we - ws;  // candidate j is a seed (or the query) iff j - ws <= wlen, unsigned
-      for (uint32_t sI = 0; sI < ns; ++sI) {
-        const uint32_t j = (sI < s0) ? j0 + 4u * sI : 4u * (sI - s0);
-        float dd[4];
+      if (uni) {
+        // forward from we + 1 to n1 (the tail reads the sentinels after P_1), then
+        // backward from ws to 0 (the last step may read the sentinels before it)
+        const uint32_t s0 = (n1 - we + 2u) >> 2, ns = s0 + ((ws + 3u) >> 2);
+        for (uint32_t sI = 0; sI < ns; ++sI) {
+          const int j = (sI < s0) ? (int)(we + 1u + 4u * sI) : (int)ws - 4 * (int)(sI - s0 + 1u);
+          float dd[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) dd[u] = sqdist(me, M.p1[j + u]);
-        const float thr = L[KMAX - 1];
+          for (int u = 0; u < 4; ++u) dd[u] = sqdist(me, M.p1[j + u]);
+          const float thr = L[KMAX - 1];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (dd[u] < thr && j + u - ws > wlen) {
-            pend[np * kLeafThreads + tid] = dd[u];
-            ++np;
+          for (int u = 0; u < 4; ++u) {
+            if (dd[u] < thr) {
+              pend[np * kLeafThreads + tid] = dd[u];
+              ++np;
+            }
+          }
+          if (__any_sync(0xFFFFFFFFu, np + 4 > pend_slots<KMAX>() || sI + 1 == ns)) {
+            merge_pending<KMAX>(L, pend, np, tid);
+            np = 0;
           }
         }
-        if (__any_sync(0xFFFFFFFFu, np + 4 > pend_slots<KMAX>() || sI + 1 == ns)) {
-          merge_pending<KMAX>(L, pend, np, tid);
-          np = 0;
+      } else {
+        // steps of 4 candidates: forward over [j0, n1 rounded up to 4) (the tail reads
+        // sentinels), then backward from j0 to 0; the last step also merges what is still parked
+        const uint32_t s0 = (n1 - j0 + 3u) >> 2, ns = s0 + (j0 >> 2);
+        const uint32_t wlen = we - ws;  // candidate j is a seed (or the query) iff j - ws <= wlen, unsigned
+        for (uint32_t sI = 0; sI < ns; ++sI) {
+          const uint32_t j = (sI < s0) ? j0 + 4u * sI : j0 - 4u * (sI - s0 + 1u);
+          float dd[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) dd[u] = sqdist(me, M.p1[j + u]);
+          const float thr = L[KMAX - 1];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (dd[u] < thr && j + u - ws > wlen) {
+              pend[np * kLeafThreads + tid] = dd[u];
+              ++np;
+            }
+          }
+          if (__any_sync(0xFFFFFFFFu, np + 4 > pend_slots<KMAX>() || sI + 1 == ns)) {
+            merge_pending<KMAX>(L, pend, np, tid);
+            np = 0;
+          }
         }
       }
       const float theta = L[KMAX - 1];
