@@ -105,6 +105,7 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
 struct LeafShared {
   uint32_t leaf;
   uint32_t n1, keff, m, keep_n, run;
+  uint32_t nless, ntied;  // Top-lambda cut: P_2 keys below / equal to the keep_n-th
   uint32_t crank;  // Eq. 14 cut rank c, from the top of the ascending r^2 order
   float lo[3], h, delta, r2ref, Lref;
   double rho_med;
@@ -842,20 +843,49 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   // Top-lambda: sort the keys (~F, input index); a point is kept iff its own key
   // is at most the keep_n-th smallest key (keys are unique).
   if (P.select_mode == DENOISE_SELECT_TOPRATIO) {
-    for (uint32_t i = tid; i < sn; i += NT) {
-      unsigned long long key = kEmpty;
-      if (i < n1 && M.flag[i])
-        key = ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | __float_as_uint(M.p1[i].w);
-      M.sbuf[i] = key;
-    }
+    // 32-bit keys ~F (F >= 0: the bit pattern orders like the value) are sorted; the
+    // keep_n-th key is the cut value; the P_2 points below it are kept, and of those
+    // at it, the ones needed to reach keep_n in input-index order (all of them
+    // unless scores tie exactly at the cut).
+    uint32_t *const kb = reinterpret_cast<uint32_t *>(M.sbuf);
+    for (uint32_t i = tid; i < sn; i += NT)
+      kb[i] = (i < n1 && M.flag[i]) ? 0xFFFFFFFFu - __float_as_uint(M.F[i]) : 0xFFFFFFFFu;
+    if (tid == 0) S.nless = S.ntied = 0;
     __syncthreads();
-    block_sort<unsigned long long>(M.sbuf, sn, kEmpty);
-    const unsigned long long cut = M.sbuf[S.keep_n - 1];
+    block_sort<uint32_t>(kb, sn, 0xFFFFFFFFu);
+    const uint32_t cut = kb[S.keep_n - 1];
+    uint32_t nl = 0, nt = 0;
     for (uint32_t i = tid; i < n1; i += NT) {
       if (!M.flag[i]) continue;
-      const unsigned long long key =
-          ((unsigned long long)(0xFFFFFFFFu - __float_as_uint(M.F[i])) << 32) | __float_as_uint(M.p1[i].w);
-      M.flag[i] = (key <= cut) ? 2 : 1;
+      const uint32_t key = 0xFFFFFFFFu - __float_as_uint(M.F[i]);
+      nl += key < cut;
+      nt += key == cut;
+    }
+    nl = __reduce_add_sync(0xFFFFFFFFu, nl);
+    nt = __reduce_add_sync(0xFFFFFFFFu, nt);
+    if (lane == 0) {
+      atomicAdd(&S.nless, nl);
+      atomicAdd(&S.ntied, nt);
+    }
+    __syncthreads();
+    const uint32_t needed = S.keep_n - S.nless, tied = S.ntied;  // 1 <= needed <= tied
+    for (uint32_t i = tid; i < n1; i += NT) {
+      if (!M.flag[i]) continue;
+      const uint32_t key = 0xFFFFFFFFu - __float_as_uint(M.F[i]);
+      bool keep = key < cut;
+      if (key == cut) {
+        if (needed >= tied) {
+          keep = true;
+        } else {  // exact score ties at the cut: rank the tied points by input index
+          const uint32_t g = __float_as_uint(M.p1[i].w);
+          uint32_t before = 0;
+          for (uint32_t j2 = 0; j2 < n1; ++j2)
+            before += (M.flag[j2] && 0xFFFFFFFFu - __float_as_uint(M.F[j2]) == cut &&
+                       __float_as_uint(M.p1[j2].w) < g);
+          keep = before < needed;
+        }
+      }
+      M.flag[i] = keep ? 2 : 1;
     }
   } else {
     for (uint32_t i = tid; i < n1; i += NT)
