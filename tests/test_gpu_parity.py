@@ -149,6 +149,35 @@ def test_lattice_ties(dn, orc):
     compare_with_oracle(g, r, P)
 
 
+def test_topratio_cut_through_exact_score_ties(dn):
+    """Two translated copies of one cluster in one leaf (max_depth 0: input
+    order is the leaf order) give bit-identical scores pairwise, so the Top-lambda
+    cut falls between points of equal F: the kept set must still be the
+    ceil(lambda m) largest by (F descending, input index ascending) (Eq. 22)."""
+    rng = np.random.default_rng(21)
+    a = rng.integers(0, 512, size=(150, 3)).astype(np.float32) / 64.0  # exact in FP32
+    a = np.unique(a, axis=0)
+    b = a + np.float32(64.0)                                           # exact translation, far apart
+    xyz = np.concatenate([a, b]).astype(np.float32)
+    n = len(xyz)
+    split_a_tie = False
+    for lam in (0.5, 0.9, 0.95):
+        P = P_(k=8, max_depth=0, leaf_capacity=n, min_vox_count=1, lam=lam)
+        res = dn.run(torch.from_numpy(xyz).cuda(), P)
+        mask, score, stage = (t.cpu().numpy() for t in (res.mask, res.score, res.stage))
+        p2 = np.where((stage == 0) | (stage == 3))[0]
+        m = len(p2)
+        keep_n = min(m, int(np.ceil(np.float64(lam) * m)))
+        F = score[p2]
+        order = np.lexsort((p2, -F.astype(np.float64)))  # F descending, then input index
+        want = np.zeros(n, np.uint8)
+        want[p2[order[:keep_n]]] = 1
+        assert np.array_equal(mask, want), lam
+        # the cut really splits a group of equal scores for at least one lambda
+        split_a_tie |= bool(keep_n < m and F[order[keep_n]] == F[order[keep_n - 1]])
+    assert split_a_tie
+
+
 # ---------------------------------------------------------------------------
 # the dense scan workload at full size (560,000 points, K = 32), as benchmarked
 # ---------------------------------------------------------------------------
