@@ -166,17 +166,6 @@ __device__ __forceinline__ uint32_t hash_insert(unsigned long long *hk, uint32_t
   return s;
 }
 
-__device__ __forceinline__ uint32_t hash_find(const unsigned long long *hk, uint32_t hcap,
-                                              unsigned long long key) {
-  const uint32_t mask = hcap - 1;
-  uint32_t s = (uint32_t)mix64(key) & mask;
-  for (uint32_t probe = 0; probe < hcap; ++probe) {
-    if (hk[s] == key) return s;
-    s = (s + 1) & mask;
-  }
-  return 0xFFFFFFFFu;
-}
-
 // Ascending bitonic sort of a[0..n) (n a power of two) by the whole block, one
 // compare-exchange stage per barrier: the general form, for any n.
 template <typename T>
@@ -439,6 +428,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   }
   __syncthreads();
   const float lo0 = S.lo[0], lo1 = S.lo[1], lo2 = S.lo[2], h = S.h;
+  // each point's hash slot, for the gate below (wa is idle until the score weights)
+  uint32_t *const vslot = reinterpret_cast<uint32_t *>(M.wa);
   for (uint32_t base = 0; base < nt; base += NT) {
     const uint32_t i = base + tid;
     unsigned long long key = kInvalid;
@@ -448,10 +439,13 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
             ((unsigned long long)vox_index(p.y, lo1, h) << 21) | (unsigned long long)vox_index(p.z, lo2, h);
     }
     const uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
+    uint32_t sl = 0;
     if (i < nt && (peers & lt) == 0) {
-      const uint32_t s = hash_insert(M.hkey, hcap, key, A.ctr);
-      atomicAdd(M.hcnt + s, (uint32_t)__popc(peers));
+      sl = hash_insert(M.hkey, hcap, key, A.ctr);
+      atomicAdd(M.hcnt + sl, (uint32_t)__popc(peers));
     }
+    sl = __shfl_sync(0xFFFFFFFFu, sl, __ffs(peers) - 1);  // the group's first lane inserted
+    if (i < nt) vslot[i] = sl;
   }
   __syncthreads();
   // lookup, gate, compaction of P_1 (order preserved)
@@ -468,11 +462,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         atomicOr(&A.ctr->status, kStInternal);
         g = 0;
       }
-      const unsigned long long key = ((unsigned long long)vox_index(p.x, lo0, h) << 42) |
-                                     ((unsigned long long)vox_index(p.y, lo1, h) << 21) |
-                                     (unsigned long long)vox_index(p.z, lo2, h);
-      const uint32_t s = hash_find(M.hkey, hcap, key);
-      const uint32_t c = (s == 0xFFFFFFFFu) ? 0u : M.hcnt[s];
+      const uint32_t c = M.hcnt[vslot[i]];
       in1 = c >= P.min_vox_count;
       if ((kRec && A.use_dbg)) {
         if (A.dbg.vox_count) A.dbg.vox_count[g] = c;
