@@ -830,8 +830,6 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   }
   __syncthreads();
   // ---- selection: Top-lambda per leaf by (F desc, input index asc), or ln F >= tau.
-  // Top-lambda: sort the keys (~F, input index); a point is kept iff its own key
-  // is at most the keep_n-th smallest key (keys are unique).
   if (P.select_mode == DENOISE_SELECT_TOPRATIO) {
     // 32-bit keys ~F (F >= 0: the bit pattern orders like the value) are sorted; the
     // keep_n-th key is the cut value; the P_2 points below it are kept, and of those
