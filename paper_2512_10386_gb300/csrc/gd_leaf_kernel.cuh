@@ -801,29 +801,37 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       unsigned long long r_acc = 0;
       uint32_t r_n = 0;
       const uint32_t r_mask = (1u << nbB) - 1u;
-      auto term = [&](uint32_t t) {  // called for t = 0, 1, ... in order
-        uint32_t j;
+      auto next_j = [&](uint32_t t, bool valid) -> uint32_t {  // called for t = 0, 1, ... in order
         if constexpr (kPacked) {
-          if (r_n < nbB) {
+          if (valid && r_n < nbB) {
             r_acc |= (unsigned long long)(*nbr_i++) << r_n;
             r_n += 32;
           }
-          j = (uint32_t)r_acc & r_mask;
+          const uint32_t j = (uint32_t)r_acc & r_mask;
           r_acc >>= nbB;
           r_n -= nbB;
+          return j;
         } else {
-          j = (uint32_t)nbr[(size_t)t * M.cap + i];
+          return valid ? (uint32_t)nbr[(size_t)t * M.cap + i] : 0u;
         }
+      };
+      auto term = [&](uint32_t j) {
         const float d2 = sqdist(me, M.p1[j]);
         const float wt = ex2_hw(__fmaf_rn(-d2, ci, __fadd_rn(ai, M.wa[j])));  // w_den * w_dis (Eq. 17, 19)
         const float D = g2 ? d2 : pow_half_gamma(d2, hg);                    // (d^2)^(gamma/2)
         return __fmul_rn(wt, rcp_hw(__fadd_rn(D, ek)));                    // kernel of Eq. 20
       };
+      // two ranks per step (two independent chains); with k_eff odd the last step's
+      // second term is computed on the first neighbour again and dropped
 #pragma unroll 1
-      for (uint32_t t = 0; t < keff; ++t) {  // one copy of the term's code
-        const float e = term(t);
-        if (t & 1u) F1 = __fadd_rn(F1, e);
-        else F0 = __fadd_rn(F0, e);
+      for (uint32_t t = 0; t < keff; t += 2) {
+        const bool two = t + 1 < keff;
+        const uint32_t ja = next_j(t, true);
+        uint32_t jb = next_j(t + 1, two);
+        jb = two ? jb : ja;
+        const float e0 = term(ja), e1 = term(jb);
+        F0 = __fadd_rn(F0, e0);
+        if (two) F1 = __fadd_rn(F1, e1);
       }
       M.F[i] = __fadd_rn(F0, F1);
     }
