@@ -331,9 +331,9 @@ __device__ __forceinline__ void regsort_f(float (&L)[N]) {
   }
 }
 
-// Merge the lane's np (<= kPend) parked values (column `tid` of `pend`) into the
-// ascending list L: sort them (padded with +inf), take min(L[KMAX-kPend+i],
-// B[kPend-1-i]) (a bitonic sequence holding the KMAX smallest), then restore the
+// Merge the lane's np (<= NP = pend_slots<KMAX>()) parked values (column `tid` of
+// `pend`) into the ascending list L: sort them (padded with +inf), take
+// min(L[KMAX-NP+i], B[NP-1-i]) (a bitonic sequence holding the KMAX smallest), then restore the
 // order with a half-cleaner cascade.
 template <int KMAX>
 __device__ __forceinline__ void merge_pending(float (&L)[KMAX], const float *pend, uint32_t np, uint32_t tid) {
@@ -515,21 +515,22 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   // ---- kNN on P_1 (excluding self), order by (d^2, input index): one thread per query.
   // Phase A finds theta, the k_eff-th smallest d^2, in a sorted register list of
   // FP32 values (placeholders -1 fill the unused KMAX - k_eff slots).  The list
-  // is seeded with the k_eff Morton-order neighbours of the query (window
-  // [ws, we]) and sorted once by a register bitonic network.  The scan then
-  // broadcasts the other candidates from shared memory to the warp, four per
-  // step (four independent distance chains); a lane whose candidate beats its
-  // current k-th value parks it in its column of a small shared buffer, and
-  // once some lane could overflow its kPend slots at the next step the warp
-  // merges the parked values into the lists (sort of kPend values + bitonic
-  // merge), so the list update is paid once per batch, not per insertion.
-  // Phase B rescans all candidates (four per step): every d^2 < theta is kept;
+  // is seeded with k_eff Morton-order neighbours of the query (window [ws, we])
+  // and sorted once by a register sorting network.  The scan then broadcasts the
+  // other candidates from shared memory to the warp, four per step (four
+  // independent distance chains); a lane whose candidate beats its current k-th
+  // value parks it in its column of a small shared buffer, and once some lane
+  // could overflow its slots at the next step the warp merges the parked values
+  // into the lists (sort of the slots + bitonic merge), so the list update is
+  // paid once per batch, not per insertion.
+  // Phase B rescans all candidates by chunks of 32: every d^2 < theta is kept;
   // the candidates at exactly theta are counted and, when exactly as many ties
   // as needed exist, all kept.  Otherwise (exact lattices, duplicates) extra
   // scans take the ties in input-index order.  The set is the k_eff smallest by
   // (d^2, input index), as with a full sort.
   {
-    // parked candidates live in the sort buffer, idle during the kNN (kPend columns of kLeafThreads)
+    // parked candidates live in the sort buffer and wa, both idle during the kNN
+    // (pend_slots<KMAX>() columns of kLeafThreads)
     float *const pend = reinterpret_cast<float *>(M.sbuf);
     const float delta2 = __fmul_rn(S.delta, S.delta);
     const uint32_t cap = M.cap;
