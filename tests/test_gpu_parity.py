@@ -140,11 +140,13 @@ def test_degenerate_clouds(dn, orc):
         compare_with_oracle(g, r, P)
 
 
-def test_lattice_ties(dn, orc):
+@pytest.mark.parametrize("k", [8, 32])
+def test_lattice_ties(dn, orc, k):
+    """Exact distance ties everywhere; k = 32 also takes the warp-shared seed window."""
     g1 = np.arange(9, dtype=np.float32) * 0.5
     xyz = np.stack(np.meshgrid(g1, g1, g1, indexing="ij"), -1).reshape(-1, 3)
     xyz = xyz[np.random.default_rng(3).permutation(len(xyz))]
-    P = P_(k=8, leaf_capacity=100, min_vox_count=1)
+    P = P_(k=k, leaf_capacity=100, min_vox_count=1)
     g, r = run_both(dn, orc, xyz, P)
     compare_with_oracle(g, r, P)
 
