@@ -92,6 +92,16 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Device address of pinned (page-locked, mapped) host memory, or null for anything else.
+const float *mapped_host(const float *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? static_cast<const float *>(at.devicePointer) : nullptr;
+}
+
 int check_params(const denoise_params *p) {
   if (!p) return DENOISE_E_INVAL;
   if (p->k == 0 || p->k > 64) return DENOISE_E_INVAL;
@@ -177,7 +187,11 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
             uint8_t *mask, float *score, uint8_t *stage, const denoise_debug *dbg, bool use_events,
             cudaStream_t st, const float *xyz_host, uint8_t *mask_h, float *score_h, uint8_t *stage_h) {
   int launches = 0;
-  if (xyz_host) {
+  // Pinned host input is read in place by the bounding-box pass, which writes the
+  // device copy on the way (one pass over the link, overlapped with the reduction);
+  // other host memory is copied first.
+  const float *xyz_mapped = xyz_host ? mapped_host(xyz_host) : nullptr;
+  if (xyz_host && !xyz_mapped) {
     if (cudaMemcpyAsync(c->d_xyz, xyz_host, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, st) !=
         cudaSuccess)
       return cuda_fail();
@@ -187,6 +201,8 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
   if (use_events) cudaEventRecord(c->ev[0], st);
   FrontArgs fa{};
   fa.xyz = xyz_dev;
+  fa.xyz_src = xyz_mapped;
+  fa.xyz_copy = xyz_mapped ? c->d_xyz : nullptr;
   fa.n = n;
   fa.frames = c->d_frames;
   fa.nframes = nframes;

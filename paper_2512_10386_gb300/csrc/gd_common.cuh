@@ -140,7 +140,9 @@ __device__ __forceinline__ unsigned long long morton3(uint32_t qx, uint32_t qy, 
 
 // Host-side launch helpers (defined in gd_front.cu / gd_leaf.cu).
 struct FrontArgs {
-  const float *xyz;
+  const float *xyz;       // device copy of the points, read after the bounding-box pass
+  const float *xyz_src;   // where the bounding-box pass reads them (null: xyz); may be mapped pinned host memory
+  float *xyz_copy;        // if set, the bounding-box pass also writes what it read here (= xyz)
   uint32_t n;
   FrameInfo *frames;
   uint32_t nframes;

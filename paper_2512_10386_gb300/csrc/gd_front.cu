@@ -48,6 +48,7 @@ __global__ void k_init(FrameInfo *frames, uint32_t nframes, Counters *ctr, uint3
 // flags non-finite coordinates.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kFrontThreads) k_bbox(const float *__restrict__ xyz,
+                                                        float *__restrict__ xyz_copy,
                                                         FrameInfo *frames, const Tile *__restrict__ tiles,
                                                         Counters *ctr) {
   pdl_wait();
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_bbox(const float *__restrict_
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const float v = xyz[3ull * i + a];
+        if (xyz_copy) xyz_copy[3ull * i + a] = v;  // host input read in place: the device copy
         bad |= !isfinite(v);
         const uint32_t o = f2ord(v);
         mn[a] = min(mn[a], o);
@@ -544,7 +546,8 @@ int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t
     launch_pdl(k_init, blocks, 256, 0, st, a.frames, a.nframes, a.ctr, a.digit_hist, a.lookback, nlb, passes);
     ++nl;
   }
-  launch_pdl(k_bbox, a.ntiles, kFrontThreads, 0, st, a.xyz, a.frames, a.tiles, a.ctr);
+  launch_pdl(k_bbox, a.ntiles, kFrontThreads, 0, st, a.xyz_src ? a.xyz_src : a.xyz, a.xyz_copy, a.frames, a.tiles,
+             a.ctr);
   launch_pdl(k_keys, a.ntiles, kFrontThreads, 0, st, a.xyz, a.frames, a.tiles, a.keys[0], a.vals[0], a.dbg_key,
                                              a.digit_hist, lowbit, passes, a.ctr);
   nl += 2;
