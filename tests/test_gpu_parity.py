@@ -206,6 +206,20 @@ def test_host_buffers_match_device_buffers(dn):
     assert torch.equal(rd.stage.cpu(), rh.stage)
 
 
+def test_pageable_host_input_matches_device_input(dn):
+    """Pinned host input is read in place by the bounding-box pass; pageable host
+    memory takes the copy-first path: both give the device-input results."""
+    import synth
+    xyz, _ = synth.object_cloud(seed=11, n_surface=5000)
+    P = P_(k=16)
+    rd = dn.run(torch.from_numpy(xyz).cuda(), P)
+    src = torch.from_numpy(xyz.copy())  # pageable
+    assert not src.is_pinned()
+    rp = dn.run(src, P)
+    assert torch.equal(rd.mask.cpu(), rp.mask.cpu()) and torch.equal(rd.score.cpu(), rp.score.cpu())
+    assert torch.equal(rd.stage.cpu(), rp.stage.cpu())
+
+
 def test_deterministic_bytes(dn):
     import synth
     xyz, _ = synth.object_cloud(seed=10, n_surface=20000)
