@@ -17,10 +17,12 @@ Extra objects on the line:
                 library's per-stage CUDA events; FP32 work = 8 flop per
                 candidate pair (3 sub + 1 mul + 2 fma of d^2)
   e2e           the same metric through the public call with pinned HOST
-                buffers, copies included
+                buffers, host-device transfers included
   cpu_baseline  the FP64 oracle on the host's CPU cores, bounded sample
   batched       64 LiDAR frames (60k-130k points) as one graph-captured batch,
                 against the same frames one call each
+  serving       a Poisson 20 Hz stream through the continuous-batching server
+                (latency p50/p99), and the same frames all at once
 ``--impl reference`` times the FP64 oracle instead (the reference arm).
 """
 
