@@ -131,6 +131,19 @@ def test_max_depth_zero_single_leaf(dn, orc):
     compare_with_oracle(g, r, P)
 
 
+@pytest.mark.parametrize("n", [2, 32, 33, 34, 35, 37, 64, 65, 97, 130])
+def test_single_leaf_scan_edges(dn, orc, n):
+    """One leaf of n points at K = 32: the whole leaf as the seed window (n <= 33),
+    one forward step into the NaN padding (34..37), backward steps that start
+    below position 0, and several query rounds."""
+    rng = np.random.default_rng(n)
+    xyz = rng.normal(size=(n, 3)).astype(np.float32)
+    P = P_(k=32, leaf_capacity=n, max_depth=0, min_vox_count=1)
+    g, r = run_both(dn, orc, xyz, P)
+    assert r["n_leaves"] == 1
+    compare_with_oracle(g, r, P)
+
+
 def test_degenerate_clouds(dn, orc):
     for xyz in (np.zeros((1, 3), np.float32), np.ones((2, 3), np.float32), np.ones((700, 3), np.float32),
                 np.stack([np.arange(300, dtype=np.float32), np.zeros(300, np.float32),
