@@ -542,10 +542,11 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       const uint32_t qq = act ? q : n1 - 1;          // idle lanes shadow a real query, results discarded
       const float4 me = M.p1[qq];
       const uint32_t j0 = qb + w * 32;               // < n1: lane 0 of a busy warp is busy
-      // Seed window [ws, we] (k_eff + 1 positions holding the query): with k_eff >= 32
-      // one window for the whole warp (it holds the warp's 32 queries), so that the
-      // scan needs no per-lane window test; otherwise centred on the lane's query.
-      const bool uni = keff >= 32u;
+      // Seed window [ws, we] (k_eff + 1 positions holding the query): with k_eff >= 32,
+      // or when it is the whole leaf, one window for the whole warp (it holds the
+      // warp's 32 queries), so that the scan needs no per-lane window test; otherwise
+      // centred on the lane's query.
+      const bool uni = keff >= 32u || keff + 1u == n1;  // a whole-leaf window serves the warp too
       const uint32_t half = keff / 2;
       uint32_t ws = uni ? j0 : ((qq > half) ? qq - half : 0u);
       if (ws > n1 - 1 - keff) ws = n1 - 1 - keff;
