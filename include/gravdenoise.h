@@ -16,8 +16,11 @@
  *  - Points are float32 xyz, array-of-structures [n][3] (12 bytes a point).
  *  - Buffers may be host or device pointers; the library detects which
  *    (cudaPointerGetAttributes).  Host buffers are staged through the
- *    context's device memory with asynchronous copies on the given stream;
- *    pinned host memory makes those copies truly asynchronous.
+ *    context's device memory, in stream order on the given stream: pinned
+ *    (page-locked, mapped) host input is read in place by the first kernel,
+ *    which writes the device copy; other host input is copied first; host
+ *    outputs are copied back at the end of the call.  Pinned host memory
+ *    keeps all of it asynchronous.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  All work
  *    of a call is ordered on that stream.
  *  - The caller owns every buffer it passes; the context owns all scratch.
