@@ -499,6 +499,41 @@ def run_serving(args):
             "realtime": live, "all_at_once": burst}
 
 
+def run_batch_profile(args):
+    """The batched LiDAR workload alone (64 frames, K = 24, leaf capacity 128,
+    64-thread leaf CTAs: the autotuner's usual pick), W + K graph-captured
+    batches, for profiling the leaf kernel on it; prints one JSON line."""
+    import dataclasses
+
+    import torch
+
+    import synth
+    from paper_2512_10386_gb300 import Denoiser, Params
+    from paper_2512_10386_gb300 import _native as N
+    frames = synth.lidar_batch(n_frames=args.frames)
+    offs = np.cumsum([0] + [len(f[0]) for f in frames]).tolist()
+    xyz = torch.from_numpy(np.concatenate([f[0] for f in frames])).cuda()
+    d = Denoiser(max_points=int(offs[-1]), max_frames=len(frames))
+    d.set_tuning(0, 0, 64)
+    d.set_graphs(True)
+    P = dataclasses.replace(Params(k=24), leaf_capacity=128)
+    stream = torch.cuda.Stream()
+    ms = []
+    for s in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        d.run_batch(xyz, offs, P, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        if s >= args.warmup:
+            ms.append(a.elapsed_time(b))
+    N.check(d.status(stream), "denoise_run_batch")
+    d.close()
+    print(json.dumps({"workload": f"{len(frames)} LiDAR frames, {offs[-1]} points, K=24, capacity 128",
+                      "batch_ms": ms}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -509,11 +544,15 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serving-frames", type=int, default=100)
+    ap.add_argument("--batch-profile", action="store_true",
+                    help="run only the batched LiDAR workload at fixed knobs (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_profile:
+        return run_batch_profile(args)
     return run_ours(args)
 
 
