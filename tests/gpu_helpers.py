@@ -2,7 +2,7 @@
 
 import numpy as np
 
-SCORE_RTOL = 1e-5   # spec tolerance for scores (FP32 GPU vs FP64 oracle)
+SCORE_RTOL = 1e-5   # tolerance for scores (FP32 GPU vs FP64 oracle), relative
 
 
 def oracle_params(P):
