@@ -40,6 +40,13 @@ MUTATIONS = [
     ("Top-lambda floor", "double want = ceil((double)p->lambda * (double)m2);",
      "double want = floor((double)p->lambda * (double)m2);"),
     ("cube root 3 Newton steps", "for (int it = 0; it < 10; ++it) {", "for (int it = 0; it < 3; ++it) {"),
+    ("threshold log -> log10", "(log(rk[t].f) >= (double)p->tau)", "(log10(rk[t].f) >= (double)p->tau)"),
+    ("threshold >= -> >", "(log(rk[t].f) >= (double)p->tau)", "(log(rk[t].f) > (double)p->tau)"),
+    ("threshold on F, not ln F", "(log(rk[t].f) >= (double)p->tau)", "(rk[t].f >= (double)p->tau)"),
+    ("soft removal on F, not ln F (gradient kept consistent)",
+     ("double z = (log(F[i]) - tau) / T;", "double dr_dF = -dm[i] / F[i];"),
+     ("double z = (F[i] - tau) / T;", "double dr_dF = -dm[i];")),
+    ("soft removal sign of tau", "double z = (log(F[i]) - tau) / T;", "double z = (log(F[i]) + tau) / T;"),
     ("voxel origin shifted", "float d = coord(c, idx[t], a) - lo[a];", "float d = coord(c, idx[t], a) - lo[a] + h * 0.5f;"),
 ]
 
@@ -47,12 +54,16 @@ MUTATIONS = [
 @pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
 def test_pins_catch_planted_mistake(tmp_path, name, old, new):
     src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
-    assert old in src, f"mutation site for '{name}' no longer exists"
+    olds, news = (old, new) if isinstance(old, tuple) else ((old,), (new,))
+    for o in olds:
+        assert o in src, f"mutation site for '{name}' no longer exists"
     for sub in ("oracle", "tests", "synth", "paper_2512_10386_gb300"):
         shutil.copytree(os.path.join(ROOT, sub), tmp_path / sub,
                         ignore=shutil.ignore_patterns("*.so", "__pycache__", "_build"))
     shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path)
-    (tmp_path / "oracle" / "oracle.c").write_text(src.replace(old, new, 1))
+    for o, n in zip(olds, news):
+        src = src.replace(o, n, 1)
+    (tmp_path / "oracle" / "oracle.c").write_text(src)
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
                         "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True,
                        timeout=600)

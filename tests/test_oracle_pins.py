@@ -381,6 +381,74 @@ def test_scaling_law(orc):
 
 
 # --------------------------------------------------------------------------
+# THRESHOLD selection (ln F >= tau) and the soft removal of the differentiable form
+# --------------------------------------------------------------------------
+def _unit_weight_pairs(orc, tau, **kw):
+    """Pairs cloud with K = 1, alpha = 0 (w_den = 1 exactly), sigma = 1e19 (the
+    distance weight exp(-1/(2 sigma^2)) rounds to 1 exactly in FP64), gamma = 2,
+    eps_k = 0: each pair's score is F = 1/s^2 exactly, so ln F = -2 ln s, and the
+    pair at s = 1 scores F = 1, ln F = 0 exactly."""
+    xyz = _pairs_cloud()
+    p = _params(orc, k=1, min_vox_count=1, rho_percentile=0.0, alpha=0.0, sigma=1e19, gamma=2.0,
+                eps_k=0.0, eps_rho=0.0, select_mode=1, tau=tau, **kw)
+    return xyz, p
+
+
+def test_threshold_selection_closed_form(orc):
+    # F = 4, 16/9, 1, 0.64 for s = 0.5, 0.75, 1, 1.25 -> ln F = 1.386, 0.575, 0, -0.446
+    want_F = [1.0 / s ** 2 for s in SEPS]
+    for tau, kept in ((0.0, [True, True, True, False]),    # ln F >= 0 keeps F = 1 (>= not >)
+                      (1.0, [True, False, False, False]),  # log10 F = 0.60 < 1 would drop s = 0.5
+                      (0.5, [True, True, False, False]),   # F >= 0.5 would keep every pair
+                      (-0.45, [True, True, True, True]),
+                      (2.0, [False, False, False, False])):
+        xyz, p = _unit_weight_pairs(orc, tau)
+        r = orc.denoise(xyz, p)
+        for i, s in enumerate(SEPS):
+            for j in (2 * i, 2 * i + 1):
+                assert r["score"][j] == want_F[i]
+                assert bool(r["mask"][j]) == kept[i], (tau, s)
+                assert r["stage"][j] == (0 if kept[i] else 3)
+    # tau just above / below each pair's ln F flips exactly that pair
+    for i, s in enumerate(SEPS):
+        lnF = float(np.log(want_F[i]))
+        for d, keep in ((1e-3, False), (-1e-3, True)):
+            xyz, p = _unit_weight_pairs(orc, lnF + d)
+            r = orc.denoise(xyz, p)
+            assert bool(r["mask"][2 * i]) == keep and bool(r["mask"][2 * i + 1]) == keep
+
+
+def test_soft_removal_closed_form(orc):
+    # r_i = 1 - sigmoid((ln F_i - tau)/T) on P_2: with ln F = -2 ln s this is
+    # 1/(1 + exp((-2 ln s - tau)/T)); the s = 1 pair at tau = 0 sits at exactly 0.5
+    T = 0.5
+    for tau in (0.0, 0.3):
+        xyz, p = _unit_weight_pairs(orc, tau, temperature=T)
+        noise = np.zeros(len(xyz), np.uint8)
+        noise[-2:] = 1
+        loss, grad, rem = orc.softf1(xyz, p, noise)
+        for i, s in enumerate(SEPS):
+            z = (-2.0 * np.log(s) - _f32(tau)) / T
+            want = 1.0 / (1.0 + np.exp(z))
+            assert abs(rem[2 * i] - want) <= 1e-12 and abs(rem[2 * i + 1] - want) <= 1e-12
+        if tau == 0.0:
+            assert rem[4] == 0.5 and rem[5] == 0.5
+        # soft F1 of Eq. 26-28 with soft removal counts
+        want_loss = 1 - 2 * (rem * noise).sum() / (rem.sum() + noise.sum())
+        assert abs(loss - want_loss) <= 1e-12
+    # points removed by a gate count as removed with probability 1
+    xyz, p = _unit_weight_pairs(orc, 0.0, temperature=T)
+    xyz = np.concatenate([xyz, np.array([[0.0, 60.0, 0.0]], np.float32)])
+    p.min_vox_count = 2
+    p.beta = 0.5
+    r = orc.denoise(xyz, p)
+    assert r["stage"][-1] == 1
+    noise = np.zeros(len(xyz), np.uint8)
+    _, _, rem = orc.softf1(xyz, p, noise)
+    assert rem[-1] == 1.0
+
+
+# --------------------------------------------------------------------------
 # invariants and special cases of the whole pipeline
 # --------------------------------------------------------------------------
 def test_permutation_invariance(orc):
