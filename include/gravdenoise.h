@@ -78,9 +78,13 @@ typedef struct denoise_ctx denoise_ctx;
 /*
  * Create a context on CUDA device `device` able to process up to
  * `max_points` points in one call, split into at most `max_frames` frames.
- * All device scratch (sort buffers, octree leaf table, per-leaf spill space)
- * is allocated here, sized for max_points; no later call allocates device
- * memory.  *out receives the context (NULL on failure).
+ * All device scratch of the forward path (sort buffers, octree leaf table,
+ * per-leaf spill space) is allocated here, sized for max_points; the forward
+ * calls (denoise_run, denoise_run_batch, denoise_run_debug) allocate no device
+ * memory.  The one later allocation is the training cache, made by the first
+ * denoise_set_training(ctx, 1) (about 520 bytes a point).  The largest buffer
+ * is allocated first, so a context too large for the GPU fails with E_NOMEM
+ * before it holds any memory.  *out receives the context (NULL on failure).
  * Errors: E_INVAL (out NULL, max_points or max_frames 0), E_NOMEM, E_CUDA.
  */
 int denoise_create(denoise_ctx **out, int device, size_t max_points, uint32_t max_frames);
@@ -152,6 +156,27 @@ typedef struct denoise_tuning {
 } denoise_tuning;
 int denoise_set_tuning(denoise_ctx *ctx, const denoise_tuning *t);
 
+/*
+ * Bounded device-side waits.  Two waits in the path can spin: a radix-sort
+ * tile waiting for its predecessor's published prefix (decoupled look-back)
+ * and the leaf kernel waiting for its bulk copy of a leaf.  Each gives up after
+ * `iterations` polls (0 = the built-in limit, 2^22), sets the call's status to
+ * DENOISE_E_TIMEOUT and returns, so the call ends and the context stays usable.
+ * Errors: E_INVAL for a NULL context.
+ */
+int denoise_set_wait_limit(denoise_ctx *ctx, uint32_t iterations);
+
+/*
+ * Test hook for the timeout path (no paper counterpart; off by default).  With
+ * tile >= 0, tile `tile` of the first radix-sort pass of every later call on
+ * this context never publishes its look-back prefix, so the tile after it waits
+ * until the wait limit (denoise_set_wait_limit) runs out and the call returns
+ * DENOISE_E_TIMEOUT with void results.  No memory is touched out of bounds and
+ * nothing waits without a limit.  tile = -1 turns the hook off.
+ * Errors: E_INVAL for a NULL context or tile < -1.
+ */
+int denoise_test_hold_lookback(denoise_ctx *ctx, int32_t tile);
+
 /* Wait for the context's last call on `stream` and return its device-side
  * status (DENOISE_OK, E_NONFINITE or E_TIMEOUT). */
 int denoise_get_status(denoise_ctx *ctx, void *stream);
@@ -219,7 +244,8 @@ int denoise_backward(denoise_ctx *ctx, const float *grad_removal, double *grad4,
  * file-scope device array of the library (7,619,328 bytes per GPU, held by every
  * GPU that loads the library until the process exits).  Nothing is allocated:
  * no context, no cudaMalloc/cudaFree, no pinned memory.
- *  xyz   [n][3] float32, DEVICE pointer (host pointers are rejected).
+ *  xyz   [n][3] float32, DEVICE pointer of the current GPU (host pointers and
+ *        pointers of another GPU are rejected).
  *  mask, score, stage: as denoise_run, DEVICE pointers or NULL.
  *  Works on the calling thread's current CUDA device.  The first call on a
  *  device looks up the scratch array's device address (cudaGetSymbolAddress);

@@ -32,6 +32,7 @@ EXPORTED = [
     "denoise_set_sync", "denoise_set_graphs", "denoise_set_profiling", "denoise_get_status",
     "denoise_get_stats", "denoise_run_debug", "denoise_set_training", "denoise_soft_removal",
     "denoise_backward", "denoise_run_noalloc", "denoise_set_tuning", "denoise_noalloc_scratch_bytes",
+    "denoise_set_wait_limit", "denoise_test_hold_lookback",
 ]
 DENOISE_NOALLOC_MAX_POINTS = 16384
 
@@ -113,6 +114,8 @@ def lib():
     L.denoise_backward.argtypes = [_V, _V, ctypes.POINTER(ctypes.c_double), _V]
     L.denoise_run_noalloc.argtypes = [_V, ctypes.c_size_t, _P, _V, _V, _V, _V]
     L.denoise_set_tuning.argtypes = [_V, ctypes.POINTER(denoise_tuning)]
+    L.denoise_set_wait_limit.argtypes = [_V, ctypes.c_uint32]
+    L.denoise_test_hold_lookback.argtypes = [_V, ctypes.c_int32]
     for name in EXPORTED:
         if name != "denoise_strerror":
             getattr(L, name).restype = ctypes.c_int
@@ -185,6 +188,14 @@ def denoise_set_training(ctx, on: int) -> int:
 def denoise_set_tuning(ctx, leaf_ctas_per_sm: int = 0, leaf_smem_points: int = 0, leaf_threads: int = 0) -> int:
     return lib().denoise_set_tuning(ctx, ctypes.byref(denoise_tuning(leaf_ctas_per_sm, leaf_smem_points,
                                                                      leaf_threads)))
+
+
+def denoise_set_wait_limit(ctx, iterations: int) -> int:
+    return lib().denoise_set_wait_limit(ctx, int(iterations))
+
+
+def denoise_test_hold_lookback(ctx, tile: int) -> int:
+    return lib().denoise_test_hold_lookback(ctx, int(tile))
 
 
 def denoise_get_status(ctx, stream) -> int:

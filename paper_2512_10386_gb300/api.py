@@ -94,6 +94,14 @@ class Denoiser:
         N.check(N.denoise_set_tuning(self.ctx, int(leaf_ctas_per_sm), int(leaf_smem_points), int(leaf_threads)),
                 "denoise_set_tuning")
 
+    def set_wait_limit(self, iterations: int):
+        """Polls before a bounded device wait gives up (``denoise_set_wait_limit``; 0 = built-in)."""
+        N.check(N.denoise_set_wait_limit(self.ctx, int(iterations)), "denoise_set_wait_limit")
+
+    def test_hold_lookback(self, tile: int):
+        """Test hook (``denoise_test_hold_lookback``): radix tile ``tile`` never publishes; -1 = off."""
+        N.check(N.denoise_test_hold_lookback(self.ctx, int(tile)), "denoise_test_hold_lookback")
+
     def set_training(self, on: bool):
         N.check(N.denoise_set_training(self.ctx, on), "denoise_set_training")
 

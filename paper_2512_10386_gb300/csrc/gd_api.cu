@@ -59,6 +59,8 @@ struct denoise_ctx {
   uint32_t leaf_ctas_per_sm = 0;
   uint32_t leaf_smem_points = 0;
   uint32_t leaf_threads = 0;
+  uint32_t wait_limit = 0;   // bounded device waits (0 = built-in limit)
+  uint32_t hold_tile1 = 0;   // test hook of the radix look-back (0 = off)
   // last call
   size_t last_n = 0;
   uint32_t last_nframes = 0;
@@ -82,14 +84,20 @@ namespace {
 
 constexpr size_t kBackPartials = 1024;
 
-bool is_device_ptr(const void *p) {
-  if (!p) return false;
+// Where a caller's buffer lives: host memory (staged through the context), device
+// memory of the context's GPU, or unusable (device memory of another GPU, which
+// the kernels could not read without peer access).
+enum class Loc { kHost, kDevice, kOtherDevice };
+
+Loc locate(const void *p, int device) {
   cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return Loc::kHost;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return Loc::kDevice;
+  if (at.type == cudaMemoryTypeDevice) return at.device == device ? Loc::kDevice : Loc::kOtherDevice;
+  return Loc::kHost;
 }
 
 // Device address of pinned (page-locked, mapped) host memory, or null for anything else.
@@ -221,6 +229,8 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
   fa.dbg_key = dbg ? dbg->key : nullptr;
   fa.max_depth = (int)p.max_depth;
   fa.leaf_capacity = p.leaf_capacity;
+  fa.spin_limit = c->wait_limit;
+  fa.hold_tile1 = c->hold_tile1;
   if (launch_front(fa, st, &launches, use_events ? &c->ev[1] : nullptr, use_events ? &c->ev[2] : nullptr))
     return cuda_fail();
   if (use_events) cudaEventRecord(c->ev[3], st);
@@ -243,6 +253,7 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
   la.big_bpp = c->big_bpp;
   la.ctas_per_sm = c->leaf_ctas_per_sm;
   la.threads = c->leaf_threads;
+  la.spin_limit = c->wait_limit;
   const int kmax = leaf_kmax(p.k);
   la.lmax = leaf_pick_lmax(p.leaf_capacity, kmax, c->smem_optin - 2048);
   if (c->leaf_smem_points) {
@@ -305,16 +316,22 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
   if (c->training && !c->train_alloc) return DENOISE_E_STATE;
   if (c->training && p->k > 64) return DENOISE_E_INVAL;
 
-  // resolve host / device buffers
-  const bool xyz_dev = is_device_ptr(xyz);
+  // resolve host / device buffers (device memory of another GPU is rejected)
+  const Loc lx = locate(xyz, c->device);
+  const Loc lm = mask ? locate(mask, c->device) : Loc::kDevice;
+  const Loc ls = score ? locate(score, c->device) : Loc::kDevice;
+  const Loc lg = stage ? locate(stage, c->device) : Loc::kDevice;
+  if (lx == Loc::kOtherDevice || lm == Loc::kOtherDevice || ls == Loc::kOtherDevice || lg == Loc::kOtherDevice)
+    return DENOISE_E_INVAL;
+  const bool xyz_dev = lx == Loc::kDevice;
   const float *xyz_d = xyz_dev ? xyz : c->d_xyz;
   const float *xyz_h = xyz_dev ? nullptr : xyz;
   uint8_t *mask_d = mask, *mask_h = nullptr;
   float *score_d = score, *score_h = nullptr;
   uint8_t *stage_d = stage, *stage_h = nullptr;
-  if (mask && !is_device_ptr(mask)) { mask_h = mask; mask_d = c->d_mask; }
-  if (score && !is_device_ptr(score)) { score_h = score; score_d = c->d_score; }
-  if (stage && !is_device_ptr(stage)) { stage_h = stage; stage_d = c->d_stage; }
+  if (mask && lm == Loc::kHost) { mask_h = mask; mask_d = c->d_mask; }
+  if (score && ls == Loc::kHost) { score_h = score; score_d = c->d_score; }
+  if (stage && lg == Loc::kHost) { stage_h = stage; stage_d = c->d_stage; }
 
   // frame layout -> tiles (re-built only when it changes)
   bool layout_changed = c->layout.size() != nframes + 1 ||
@@ -345,6 +362,8 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
     put(&c->leaf_ctas_per_sm, sizeof(c->leaf_ctas_per_sm));
     put(&c->leaf_smem_points, sizeof(c->leaf_smem_points));
     put(&c->leaf_threads, sizeof(c->leaf_threads));
+    put(&c->wait_limit, sizeof(c->wait_limit));
+    put(&c->hold_tile1, sizeof(c->hold_tile1));
     put(offsets, sizeof(uint64_t) * (nframes + 1));
     if (!c->gexec || key != c->gkey) {
       if (c->gexec) {
@@ -424,7 +443,9 @@ int denoise_create(denoise_ctx **out, int device, size_t max_points, uint32_t ma
   c->big_bpp = leaf_big_bpp(64);
   const size_t N = max_points;
   int e = 0;
-  e |= dalloc(&c->d_xyz, 3 * N);
+  // largest first: a context too large for the GPU fails before it holds anything
+  e |= dalloc(&c->d_big, N * c->big_bpp);
+  if (!e) e |= dalloc(&c->d_xyz, 3 * N);
   e |= dalloc(&c->d_mask, N);
   e |= dalloc(&c->d_score, N);
   e |= dalloc(&c->d_stage, N);
@@ -442,7 +463,6 @@ int denoise_create(denoise_ctx **out, int device, size_t max_points, uint32_t ma
   e |= dalloc(&c->d_leaves, N);
   e |= dalloc(&c->d_order, N);
   e |= dalloc(&c->d_ctr, 1);
-  e |= dalloc(&c->d_big, N * c->big_bpp);
   e |= dalloc(&c->d_partials, kBackPartials * 4);
   e |= dalloc(&c->d_grad, 4);
   if (e) {
@@ -529,6 +549,18 @@ int denoise_set_tuning(denoise_ctx *ctx, const denoise_tuning *t) {
   return DENOISE_OK;
 }
 
+int denoise_set_wait_limit(denoise_ctx *ctx, uint32_t iterations) {
+  if (!ctx) return DENOISE_E_INVAL;
+  ctx->wait_limit = iterations;
+  return DENOISE_OK;
+}
+
+int denoise_test_hold_lookback(denoise_ctx *ctx, int32_t tile) {
+  if (!ctx || tile < -1) return DENOISE_E_INVAL;
+  ctx->hold_tile1 = (uint32_t)(tile + 1);
+  return DENOISE_OK;
+}
+
 int denoise_get_status(denoise_ctx *ctx, void *stream) {
   if (!ctx) return DENOISE_E_INVAL;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return DENOISE_E_CUDA;
@@ -577,7 +609,9 @@ int denoise_soft_removal(denoise_ctx *ctx, float *removal, void *stream) {
   if (!ctx->last_trained) return DENOISE_E_STATE;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return DENOISE_E_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
-  const bool dev = is_device_ptr(removal);
+  const Loc lr = locate(removal, ctx->device);
+  if (lr == Loc::kOtherDevice) return DENOISE_E_INVAL;
+  const bool dev = lr == Loc::kDevice;
   BackArgs a{};
   a.train = ctx->train;
   a.train.k = ctx->last_p.k;
@@ -608,7 +642,9 @@ int denoise_backward(denoise_ctx *ctx, const float *grad_removal, double *grad4,
     return DENOISE_OK;
   }
   const float *g = grad_removal;
-  if (!is_device_ptr(grad_removal)) {
+  const Loc lgr = locate(grad_removal, ctx->device);
+  if (lgr == Loc::kOtherDevice) return DENOISE_E_INVAL;
+  if (lgr == Loc::kHost) {
     cudaMemcpyAsync(ctx->d_gin, grad_removal, sizeof(float) * a.n, cudaMemcpyHostToDevice, st);
     g = ctx->d_gin;
   }

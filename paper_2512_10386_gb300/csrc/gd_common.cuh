@@ -159,6 +159,8 @@ struct FrontArgs {
   uint64_t *dbg_key;
   int max_depth;
   uint32_t leaf_capacity;
+  uint32_t spin_limit;      // iterations of a bounded look-back wait (0 = kSpinLimit)
+  uint32_t hold_tile1;      // test hook: tile hold_tile1 - 1 of the first radix pass never publishes (0 = off)
 };
 
 int front_passes(int max_depth);
@@ -185,6 +187,7 @@ struct LeafArgs {
   int use_train;
   uint32_t ctas_per_sm;         // 0 = occupancy limit
   uint32_t threads;             // threads per leaf CTA: 64 or 128 (0 = 128)
+  uint32_t spin_limit;          // iterations of the bounded bulk-copy wait (0 = kSpinLimit)
 };
 
 int leaf_kmax(uint32_t k);

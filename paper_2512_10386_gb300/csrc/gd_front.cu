@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
     unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout, float4 *__restrict__ pout,
     const float *__restrict__ xyz, const Tile *__restrict__ tiles, const FrameInfo *__restrict__ frames,
     const uint32_t *__restrict__ digit_base, uint32_t *__restrict__ lookback, uint32_t *tile_counter,
-    int shift, Counters *ctr) {
+    int shift, Counters *ctr, uint32_t spin_limit, uint32_t hold_tile1) {
   constexpr int W = kFrontThreads / 32;
   __shared__ uint32_t s_wcnt[W][256];  // per warp and digit: count, then exclusive prefix over warps
   __shared__ uint32_t s_base[256];     // global output base of each digit for this tile
@@ -285,10 +285,13 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
     s_doff[d] = wp + inc - run;
     uint32_t *lb = lookback + (size_t)ti * 256;
     uint32_t excl = 0;
+    // test hook (off unless the host asks): this tile never publishes, so the
+    // next tile's bounded wait runs out and the call reports a timeout
+    const bool publish = ti + 1u != hold_tile1;
     if (ti == t.first_tile) {
-      atomicExch(&lb[d], kFlagInc | run);
+      if (publish) atomicExch(&lb[d], kFlagInc | run);
     } else {
-      atomicExch(&lb[d], kFlagAgg | run);
+      if (publish) atomicExch(&lb[d], kFlagAgg | run);
       // walk back kLookAhead predecessors per round: their flags are read with
       // independent loads, then consumed in order (a not-yet-published one is
       // re-read until it is); stop at the first inclusive prefix
@@ -303,11 +306,11 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
         for (int u = 0; u < kLookAhead; ++u) {
           if (u >= cnt || done) break;
           uint32_t it = 0;
-          for (; it < kSpinLimit && !(wv[u] & (kFlagAgg | kFlagInc)); ++it) {
+          for (; it < spin_limit && !(wv[u] & (kFlagAgg | kFlagInc)); ++it) {
             if (it > 32) __nanosleep(64);
             wv[u] = ld_volatile(lookback + (size_t)(tp - u) * 256 + d);
           }
-          if (it == kSpinLimit) {
+          if (it == spin_limit) {
             atomicOr(&ctr->status, kStTimeout);
             s_fail = 1;
             done = true;
@@ -317,7 +320,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
           if (wv[u] & kFlagInc) done = true;
         }
       }
-      atomicExch(&lb[d], kFlagInc | (excl + run));
+      if (publish) atomicExch(&lb[d], kFlagInc | (excl + run));
     }
     s_base[d] = digit_base[(size_t)t.frame * kMaxPasses * 256 + d] + excl;
   }
@@ -535,6 +538,7 @@ int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t
                  cudaEvent_t *ev_after_sort) {
   const int passes = front_passes(a.max_depth);
   const int lowbit = 63 - 3 * a.max_depth;
+  const uint32_t spin = a.spin_limit ? a.spin_limit : kSpinLimit;
   const uint32_t nlb = a.ntiles * 256u;
   int nl = 0;
   {
@@ -563,11 +567,11 @@ int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t
       if (p == passes - 1) {
         launch_pdl(k_radix_pass<true>, a.ntiles, kFrontThreads, 0, st,
             a.keys[cur], a.vals[cur], a.keys[cur ^ 1], a.vals[cur ^ 1], a.spts, a.xyz, a.tiles, a.frames,
-            base, lb, &a.ctr->tile_work[p], shift, a.ctr);
+            base, lb, &a.ctr->tile_work[p], shift, a.ctr, spin, p == 0 ? a.hold_tile1 : 0u);
       } else {
         launch_pdl(k_radix_pass<false>, a.ntiles, kFrontThreads, 0, st,
             a.keys[cur], a.vals[cur], a.keys[cur ^ 1], a.vals[cur ^ 1], a.spts, a.xyz, a.tiles, a.frames,
-            base, lb, &a.ctr->tile_work[p], shift, a.ctr);
+            base, lb, &a.ctr->tile_work[p], shift, a.ctr, spin, p == 0 ? a.hold_tile1 : 0u);
       }
       cur ^= 1;
       ++nl;

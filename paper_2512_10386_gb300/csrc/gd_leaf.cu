@@ -151,22 +151,26 @@ size_t leaf_smem_bytes(uint32_t lmax, int kmax) {
   return carve<uint16_t>(nullptr, lmax, kmax, nullptr);
 }
 
-uint32_t leaf_big_bpp(int kmax) {
-  // max over spill-path leaf sizes (cap > 64) of carve<uint32_t>(cap)/cap, rounded
-  // up to a multiple of 16 so that every leaf's area starts 16-byte aligned.  The
-  // ratio is largest for small caps (fixed-size parts); beyond 2^16 points it only
-  // falls, so scanning 65..65536 bounds every size.
-  static uint32_t cached[65] = {0};
-  if (kmax <= 64 && cached[kmax]) return cached[kmax];
+namespace {
+// max over spill-path leaf sizes (cap > 64) of carve<uint32_t>(cap)/cap, rounded
+// up to a multiple of 16 so that every leaf's area starts 16-byte aligned.  The
+// ratio is largest for small caps (fixed-size parts); beyond 2^16 points it only
+// falls, so scanning 65..65536 bounds every size.
+uint32_t big_bpp_scan(int kmax) {
   size_t worst = 0;
   for (uint32_t cap = 65; cap <= 65536; ++cap) {
     const size_t b = carve<uint32_t>(nullptr, cap, kmax, nullptr);
     const size_t per = (b + cap - 1) / cap;
     if (per > worst) worst = per;
   }
-  const uint32_t bpp = (uint32_t)((worst + 15) & ~size_t(15));
-  if (kmax <= 64) cached[kmax] = bpp;
-  return bpp;
+  return (uint32_t)((worst + 15) & ~size_t(15));
+}
+}  // namespace
+
+uint32_t leaf_big_bpp(int kmax) {
+  // computed once, on first use, for the four list sizes (thread-safe static init)
+  static const uint32_t table[4] = {big_bpp_scan(8), big_bpp_scan(16), big_bpp_scan(32), big_bpp_scan(64)};
+  return table[kmax <= 8 ? 0 : kmax <= 16 ? 1 : kmax <= 32 ? 2 : 3];
 }
 
 uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit) {

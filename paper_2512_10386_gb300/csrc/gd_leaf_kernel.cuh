@@ -6,8 +6,6 @@
 
 #include <type_traits>
 
-#include <type_traits>
-
 #include "gd_common.cuh"
 
 namespace gd {
@@ -381,6 +379,16 @@ static __device__ __noinline__ float leaf_lref(float ra, float rb, uint32_t m, u
 // (d^2)^(gamma/2) for gamma != 2 (the score's common case gamma = 2 needs none): out of line
 static __device__ __noinline__ float pow_half_gamma(float d2, float hg) { return exp2f(__fmul_rn(hg, log2f(d2))); }
 
+// Debug and training outputs are indexed by a point's input index g, read from
+// the leaf's point data: it is < n whenever the sort and the leaf partition are
+// consistent.  Every such write goes through this check first (a failure voids
+// the call's results instead of writing out of bounds).
+__device__ __forceinline__ bool rec_index_ok(const LeafArgs &A, uint32_t g) {
+  if (g < A.n) return true;
+  atomicOr(&A.ctr->status, kStInternal);
+  return false;
+}
+
 template <bool kRec>
 __device__ __forceinline__ void write_point(const LeafArgs &A, uint32_t g, uint8_t mk, float sc, uint8_t st) {
   if (g >= A.n) {  // cannot happen with a consistent sort; never write out of bounds
@@ -635,11 +643,13 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         } else {
           nbr[(size_t)t * cap + qq] = (IdxT)npos;
         }
-        if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = g;
-        if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = d2;
-        if ((kRec && A.use_train)) {
-          A.train.nbr[(size_t)gq * P.k + t] = g;
-          A.train.nd2[(size_t)gq * P.k + t] = d2;
+        if (kRec && (dbg_n || dbg_d || A.use_train) && rec_index_ok(A, gq)) {
+          if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = g;
+          if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = d2;
+          if (A.use_train) {
+            A.train.nbr[(size_t)gq * P.k + t] = g;
+            A.train.nd2[(size_t)gq * P.k + t] = d2;
+          }
         }
       };
       // every d^2 < theta is a neighbour; the ntie candidates at exactly theta are
@@ -718,18 +728,20 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       }
       if (kPacked && act && nb_n > 0) nbw[nb_w] = (uint32_t)nb_acc;  // last partial word
       if (act) {
-        for (uint32_t t = keff; t < P.k; ++t) {
-          if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
-          if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = 0.0f;
-          if ((kRec && A.use_train)) {
-            A.train.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
-            A.train.nd2[(size_t)gq * P.k + t] = 0.0f;
-          }
-        }
         const float rt = (theta < delta2) ? delta2 : theta;
         M.r2[qq] = rt;
-        if ((kRec && A.use_dbg) && A.dbg.r2) A.dbg.r2[gq] = rt;
-        if ((kRec && A.use_train)) A.train.r2[gq] = rt;
+        if (kRec && (A.use_dbg || A.use_train) && rec_index_ok(A, gq)) {
+          for (uint32_t t = keff; t < P.k; ++t) {
+            if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
+            if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = 0.0f;
+            if (A.use_train) {
+              A.train.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
+              A.train.nd2[(size_t)gq * P.k + t] = 0.0f;
+            }
+          }
+          if (A.use_dbg && A.dbg.r2) A.dbg.r2[gq] = rt;
+          if (A.use_train) A.train.r2[gq] = rt;
+        }
       }
     }
   }
@@ -781,7 +793,10 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       const float r2 = M.r2[i];
       const float ell = __fsub_rn(Lref, __fmul_rn(1.5f, log2f(__fdiv_rn(r2, r2ref))));  // log2(rho_i / sqrt(rho_med^2 + eps))
       M.wa[i] = __fmul_rn(half_alpha, ell);
-      if ((kRec && A.use_train)) A.train.ell[__float_as_uint(M.p1[i].w)] = ell;
+      if (kRec && A.use_train) {
+        const uint32_t g = __float_as_uint(M.p1[i].w);
+        if (rec_index_ok(A, g)) A.train.ell[g] = ell;
+      }
     }
   }
   __syncthreads();
@@ -897,15 +912,15 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     const uint8_t f = M.flag[i];
     if (f == 0) write_point<kRec>(A, g, 0, 0.0f, 2);
     else write_point<kRec>(A, g, f == 2, M.F[i], f == 2 ? 0 : 3);
-    if ((kRec && A.use_dbg) && A.dbg.leaf_rho_med) A.dbg.leaf_rho_med[g] = rho_med;
+    if (kRec && A.use_dbg && A.dbg.leaf_rho_med && g < A.n) A.dbg.leaf_rho_med[g] = rho_med;
   }
 }
 
 // ---------------------------------------------------------------------------
 // persistent kernel
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -957,10 +972,10 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 6) k_leaf(con
             "l"(__cvta_generic_to_global(A.spts + lf.start)), "r"(bytes), "r"(bar)
             : "memory");
       }
-      const bool ok = mbar_wait(bar, phase);
+      const bool ok = mbar_wait(bar, phase, A.spin_limit);
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicOr(&A.ctr->status, kStTimeout);
-        (void)mbar_wait(bar, phase);  // let the copy in flight land before exiting
+        (void)mbar_wait(bar, phase, A.spin_limit);  // let the copy in flight land before exiting
         return;
       }
       phase ^= 1u;
@@ -989,7 +1004,9 @@ inline int launch_k(const LeafArgs &a, int num_sms, cudaStream_t st) {
       per_sm < 1)
     return -1;
   if (a.ctas_per_sm > 0 && (int)a.ctas_per_sm < per_sm) per_sm = (int)a.ctas_per_sm;
-  if (launch_pdl(k_leaf<KMAX, kRec>, num_sms * per_sm, nt, smem, st, a) != cudaSuccess) return -1;
+  LeafArgs la = a;
+  if (la.spin_limit == 0) la.spin_limit = kSpinLimit;
+  if (launch_pdl(k_leaf<KMAX, kRec>, num_sms * per_sm, nt, smem, st, la) != cudaSuccess) return -1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

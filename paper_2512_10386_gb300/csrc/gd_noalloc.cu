@@ -52,13 +52,15 @@ struct DeviceSetup {
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mu;
 
-bool dev_ptr(const void *p) {
+// device memory the kernels on `dev` can read: managed memory, or device memory
+// of that GPU (not of another GPU, which would need peer access)
+bool dev_ptr(const void *p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev);
 }
 
 int params_ok(const denoise_params *p) {
@@ -108,11 +110,12 @@ extern "C" int denoise_run_noalloc(const float *xyz, size_t n, const denoise_par
   if (!params_ok(p)) return DENOISE_E_INVAL;
   if (n > kN) return DENOISE_E_CAPACITY;
   if (n == 0) return DENOISE_OK;
-  if (!xyz || !dev_ptr(xyz)) return DENOISE_E_INVAL;
-  if ((mask && !dev_ptr(mask)) || (score && !dev_ptr(score)) || (stage && !dev_ptr(stage))) return DENOISE_E_INVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return fail_cuda();
   if (dev < 0 || dev >= kMaxDevices) return DENOISE_E_INVAL;
+  if (!xyz || !dev_ptr(xyz, dev)) return DENOISE_E_INVAL;
+  if ((mask && !dev_ptr(mask, dev)) || (score && !dev_ptr(score, dev)) || (stage && !dev_ptr(stage, dev)))
+    return DENOISE_E_INVAL;
   if (leaf_big_bpp(64) > kSpillBpp) return DENOISE_E_INVAL;  // carve no longer covers the spill stride
   DeviceSetup su;
   {

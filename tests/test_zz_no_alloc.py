@@ -57,6 +57,40 @@ def test_noalloc_matches_denoise_run_two_calls_in_a_row():
         d.close()
 
 
+def test_noalloc_spill_path_at_its_maximum_size():
+    # n at the maximum, K = 64, and leaves larger than the shared-memory path: the
+    # scratch array is filled to its size and the per-point spill region is used
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_10386_gb300 import Denoiser, Params
+    from paper_2512_10386_gb300 import _native as N
+    n = N.DENOISE_NOALLOC_MAX_POINTS
+    rng = np.random.default_rng(43)
+    xyz_np = np.concatenate([rng.normal(size=(n - 1000, 3)) * 0.05,
+                             rng.uniform(-1, 1, size=(1000, 3))]).astype(np.float32)
+    P = Params(k=64, leaf_capacity=4096, beta=3.0)
+    d = Denoiser(max_points=n)
+    try:
+        xyz = torch.from_numpy(xyz_np).cuda()
+        for _ in range(2):
+            ref = d.run(xyz, P)
+            st, mask, score, stage = _noalloc(N, xyz, P)
+            assert st == N.DENOISE_OK, N.strerror(st)
+            torch.cuda.synchronize()
+            sr, sg = ref.score.double().cpu().numpy(), score.double().cpu().numpy()
+            scored = sr > 0
+            assert scored.sum() > n // 2
+            assert np.array_equal(sr > 0, sg > 0)
+            assert np.all(np.abs(sg[scored] - sr[scored]) <= 1e-5 * sr[scored])
+            assert torch.equal(mask, ref.mask) and torch.equal(stage, ref.stage)
+        st = d.stats()
+        assert st["n_leaves"] <= 16           # leaves of thousands of points: the spill path
+    finally:
+        d.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_maximum():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
