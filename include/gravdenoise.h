@@ -241,7 +241,7 @@ int denoise_backward(denoise_ctx *ctx, const float *grad_removal, double *grad4,
  * allocation, or inside a real-time loop whose policy forbids cudaMalloc.
  * It denoises one cloud of at most DENOISE_NOALLOC_MAX_POINTS points with
  * exactly the kernels of denoise_run, but all scratch lives in one
- * file-scope device array of the library (7,619,328 bytes per GPU, held by every
+ * file-scope device array of the library (6,570,752 bytes per GPU, held by every
  * GPU that loads the library until the process exits).  Nothing is allocated:
  * no context, no cudaMalloc/cudaFree, no pinned memory.
  *  xyz   [n][3] float32, DEVICE pointer of the current GPU (host pointers and
@@ -261,7 +261,7 @@ int denoise_backward(denoise_ctx *ctx, const float *grad_removal, double *grad4,
 #define DENOISE_NOALLOC_MAX_POINTS 16384u
 int denoise_run_noalloc(const float *xyz, size_t n, const denoise_params *p, uint8_t *mask, float *score,
                         uint8_t *stage, void *stream);
-/* Size in bytes of denoise_run_noalloc's scratch array (7,619,328); 0 if the
+/* Size in bytes of denoise_run_noalloc's scratch array (6,570,752); 0 if the
  * library was built inconsistently (the array would not cover the kernels'
  * needs, and denoise_run_noalloc then fails with E_INVAL).  Host-only: needs
  * no GPU. */

@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "gd_common.cuh"
+#include "gd_knn_select.cuh"
 
 namespace gd {
 
@@ -14,17 +15,12 @@ constexpr int kLeafThreads = 128;
 constexpr int kLeafWarps = kLeafThreads / 32;
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned long long kInvalid = ~0ull - 1ull;
-constexpr uint32_t kPend = 12;  // parking slots per lane (at most): a warp merges before any lane could overflow
-// slots used for a list of KMAX values (the merge keeps the KMAX smallest of list and slots)
-template <int KMAX>
-__host__ __device__ constexpr uint32_t pend_slots() { return KMAX >= 16 ? 12u : 8u; }
-// P_1 is followed by kPad NaN points: the kNN scans run to the next multiple of 4
-// (phase A) or of 32 (phase B) without a bounds test, since a NaN distance is
-// neither below nor equal to any threshold.
+// P_1 is followed by kPad NaN points: the kNN passes read whole steps of 4, 16
+// or 32 candidates past the last one without a bounds test (a NaN distance falls
+// in no bucket, and the chunk masks drop positions past P_1).
 constexpr uint32_t kPad = 32;
-constexpr uint32_t kPadFront = 4;  // NaN points before P_1 too (a backward scan may start below 0)
-// the sort buffer also holds the parked candidates during the kNN
-constexpr size_t kPendBytes = (size_t)kPend * kLeafThreads * sizeof(float);
+// largest leaf of the shared-memory path: bit-sliced counts of the kNN hold < 2^11
+constexpr uint32_t kLeafSmemMax = 2048;
 
 __host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 __host__ __device__ __forceinline__ uint32_t pow2ceil(uint32_t x) {
@@ -34,12 +30,18 @@ __host__ __device__ __forceinline__ uint32_t pow2ceil(uint32_t x) {
 }
 
 // Per-leaf working arrays: shared memory (small leaves) or global spill (large).
+// P_1 is kept as structure of arrays (X, Y, Z, W), so that four consecutive
+// candidates come in one 16-byte load per coordinate and pair up for the
+// packed two-lane FP32 arithmetic of the distance passes.
 struct LeafMem {
-  float4 *p1;                // [cap + kPad] P_1 points (w = input index bits), then NaN sentinels; kPadFront before
+  float *X, *Y, *Z;          // [cap + kPad] P_1 coordinates, then NaN padding
+  uint32_t *W;               // [cap + kPad] input index of each P_1 point
+  float4 *raw;               // [cap] raw points of a shared-memory leaf (the bulk copy lands here)
   unsigned long long *hkey;  // [hcap] voxel hash keys
   uint32_t *hcnt;            // [hcap] voxel occupancy
   unsigned long long *sbuf;  // [scap] sort buffer
-  float *r2, *wa;            // [cap] per P_1 position: r_K^2, (alpha/2) ell
+  uint32_t *pend;            // [kSelBuf][kLeafThreads] parked boundary-bucket keys (shared memory, both paths)
+  float *r2, *wa;            // [cap] per P_1 position: r_K^2, (alpha/2) ell; wa also holds voxel hash slots
   float *F;                  // [cap] score; shares r2's storage (F_i is written after r2_i's last read)
   uint8_t *flag;             // [cap] 0 removed by density gate, 1 scored, 2 kept
   void *nbr;                 // neighbour positions: see nb_bits (shared memory) or [KMAX][cap] u32 (global)
@@ -49,7 +51,6 @@ struct LeafMem {
 // Neighbour table of the shared-memory path: query q owns nb_words(cap, kmax)
 // consecutive 32-bit words holding its neighbour positions as nb_bits(cap)-bit
 // fields, rank t at bit t * nb_bits (a 512-point leaf needs 9 bits, not 16).
-// The packing keeps a 512-point, K = 32 CTA at 35 KB: 6 CTAs per SM.
 __host__ __device__ __forceinline__ uint32_t nb_bits(uint32_t cap) {
   uint32_t b = 1;
   while ((1u << b) < cap) ++b;
@@ -61,17 +62,22 @@ __host__ __device__ __forceinline__ uint32_t nb_words(uint32_t cap, int kmax) {
 }
 
 // Layout of the per-leaf arrays.  Region A holds the voxel hash table, later
-// (the lifetimes do not overlap) the neighbour table.  The raw points of a
-// shared-memory leaf land in p1 and are compacted in place into P_1.
+// (the lifetimes do not overlap) the neighbour table.  Region R holds a
+// shared-memory leaf's raw points (voxel gate), then the parked kNN keys, then
+// the sort buffer of the order statistics.
 template <typename IdxT>
 __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t cap, int kmax, LeafMem *m) {
+  constexpr bool kSmem = sizeof(IdxT) == 2;
   const uint32_t hcap = pow2ceil(2 * cap), scap = pow2ceil(cap);
-  // region A: max(hash table, neighbour table)
   const size_t hash_end = al16((size_t)hcap * 8) + al16((size_t)hcap * 4);
-  const size_t nbr_bytes = (sizeof(IdxT) == 2) ? al16((size_t)cap * nb_words(cap, kmax) * 4)
-                                               : al16((size_t)cap * kmax * sizeof(IdxT));
-  size_t off = hash_end > nbr_bytes ? hash_end : nbr_bytes;
-  off = al16(off);
+  const size_t nbr_bytes = kSmem ? al16((size_t)cap * nb_words(cap, kmax) * 4) : al16((size_t)cap * kmax * sizeof(IdxT));
+  size_t o = al16(hash_end > nbr_bytes ? hash_end : nbr_bytes);
+  size_t rbytes = (size_t)scap * 8;
+  if (kSmem) {
+    const size_t raw = (size_t)cap * 16, park = (size_t)kSelBuf * kLeafThreads * 4;
+    if (raw > rbytes) rbytes = raw;
+    if (park > rbytes) rbytes = park;
+  }
   if (m) {
     m->hkey = (unsigned long long *)base;
     m->hcnt = (uint32_t *)(base + al16((size_t)hcap * 8));
@@ -80,18 +86,19 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
     m->scap = scap;
     m->cap = cap;
   }
-  size_t o = off;
   auto take = [&](size_t bytes) { size_t r = o; o = al16(o + bytes); return r; };
-  // the parked kNN candidates use the sort buffer and wa (idle during the kNN), adjacent here
-  const size_t wa_bytes = al16((size_t)cap * 4);
-  const size_t sneed = kPendBytes > wa_bytes ? kPendBytes - wa_bytes : 0;
-  const size_t sbytes = (size_t)scap * 8 > sneed ? (size_t)scap * 8 : sneed;
-  const size_t p1 = take((size_t)(kPadFront + cap + kPad) * 16) + kPadFront * 16, r2 = take((size_t)cap * 4);
-  const size_t sb = take(sbytes), wa = take((size_t)cap * 4);
-  const size_t fl = take((size_t)cap);
+  const size_t rr = take(rbytes);
+  const size_t soa = (size_t)(cap + kPad) * 4;
+  const size_t x = take(soa), y = take(soa), z = take(soa), w = take(soa);
+  const size_t r2 = take((size_t)cap * 4), wa = take((size_t)cap * 4), fl = take((size_t)cap);
   if (m) {
-    m->p1 = (float4 *)(base + p1);
-    m->sbuf = (unsigned long long *)(base + sb);
+    m->raw = kSmem ? (float4 *)(base + rr) : nullptr;
+    m->sbuf = (unsigned long long *)(base + rr);
+    m->pend = kSmem ? (uint32_t *)(base + rr) : nullptr;  // the spill path parks in the CTA's shared memory
+    m->X = (float *)(base + x);
+    m->Y = (float *)(base + y);
+    m->Z = (float *)(base + z);
+    m->W = (uint32_t *)(base + w);
     m->r2 = (float *)(base + r2);
     m->wa = (float *)(base + wa);
     m->F = m->r2;
@@ -280,17 +287,68 @@ __device__ __forceinline__ float rcp_hw(float x) {
 
 // squared distance with the fixed FP32 operation order of the method's reading:
 // dx = x_j - x_i;  d^2 = fma(dz, dz, fma(dy, dy, dx*dx))
-__device__ __forceinline__ float sqdist(const float4 &a, const float4 &b) {
-  const float dx = __fsub_rn(b.x, a.x), dy = __fsub_rn(b.y, a.y), dz = __fsub_rn(b.z, a.z);
+__device__ __forceinline__ float sqdist(float xi, float yi, float zi, float xj, float yj, float zj) {
+  const float dx = __fsub_rn(xj, xi), dy = __fsub_rn(yj, yi), dz = __fsub_rn(zj, zi);
   return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
+// Packed two-lane FP32 (sm_100 family): each instruction applies the same
+// round-to-nearest operation to both halves of a 64-bit register pair, with
+// subnormals kept, so a lane of the pair equals the scalar __fsub_rn /
+// __fmul_rn / __fmaf_rn bit for bit.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// d^2 from the query (packed broadcast QX = (x_i, x_i), ...) to the four
+// candidates j .. j+3 (j a multiple of 4): three 16-byte loads, six packed
+// subtractions and six packed multiply / fused multiply-adds
+__device__ __forceinline__ void sqdist4(const float *__restrict__ X, const float *__restrict__ Y,
+                                        const float *__restrict__ Z, uint32_t j, f32x2 QX, f32x2 QY, f32x2 QZ,
+                                        float (&d)[4]) {
+  const float4 x = *reinterpret_cast<const float4 *>(X + j);
+  const float4 y = *reinterpret_cast<const float4 *>(Y + j);
+  const float4 z = *reinterpret_cast<const float4 *>(Z + j);
+  const f32x2 dx0 = sub2(pk2(x.x, x.y), QX), dx1 = sub2(pk2(x.z, x.w), QX);
+  const f32x2 dy0 = sub2(pk2(y.x, y.y), QY), dy1 = sub2(pk2(y.z, y.w), QY);
+  const f32x2 dz0 = sub2(pk2(z.x, z.y), QZ), dz1 = sub2(pk2(z.z, z.w), QZ);
+  f32x2 s0 = mul2(dx0, dx0), s1 = mul2(dx1, dx1);
+  s0 = fma2(dy0, dy0, s0);
+  s1 = fma2(dy1, dy1, s1);
+  s0 = fma2(dz0, dz0, s0);
+  s1 = fma2(dz1, dz1, s1);
+  upk2(s0, d[0], d[1]);
+  upk2(s1, d[2], d[3]);
+}
+
 // ---------------------------------------------------------------------------
-// per-thread sorted register lists (all indices compile-time)
+// register sorting network (all indices compile-time)
 // ---------------------------------------------------------------------------
 // ascending sort network: Batcher's odd-even merge sort (19 comparators for 8
-// values, 191 for 32, against 24 and 240 for a bitonic sort).  The comparator
-// list is built at compile time, so every register index is a constant.
+// values, 63 for 16, 191 for 32, against 24, 80 and 240 for a bitonic sort).
+// The comparator list is built at compile time, so every register index is a
+// constant.
 template <int N>
 struct OddEvenNet {
   static constexpr int count() {
@@ -318,40 +376,15 @@ struct OddEvenNet {
   }
 };
 
+// ascending sort of N 32-bit keys in registers (the comparator table above)
 template <int N>
-__device__ __forceinline__ void regsort_f(float (&L)[N]) {
+__device__ __forceinline__ void regsort_u(uint32_t (&L)[N]) {
   constexpr OddEvenNet<N> net{};
 #pragma unroll
   for (int c = 0; c < OddEvenNet<N>::C; ++c) {
-    const float x = L[net.a[c]], y = L[net.b[c]];
-    L[net.a[c]] = fminf(x, y);
-    L[net.b[c]] = fmaxf(x, y);
-  }
-}
-
-// Merge the lane's np (<= NP = pend_slots<KMAX>()) parked values (column `tid` of
-// `pend`) into the ascending list L: sort them (padded with +inf), take
-// min(L[KMAX-NP+i], B[NP-1-i]) (a bitonic sequence holding the KMAX smallest), then restore the
-// order with a half-cleaner cascade.
-template <int KMAX>
-__device__ __forceinline__ void merge_pending(float (&L)[KMAX], const float *pend, uint32_t np, uint32_t tid) {
-  constexpr int NP = (int)pend_slots<KMAX>();
-  float B[NP];
-#pragma unroll
-  for (int i = 0; i < NP; ++i) B[i] = ((uint32_t)i < np) ? pend[i * kLeafThreads + tid] : INFINITY;
-  regsort_f<NP>(B);
-#pragma unroll
-  for (int i = 0; i < NP; ++i) L[KMAX - NP + i] = fminf(L[KMAX - NP + i], B[NP - 1 - i]);
-#pragma unroll
-  for (int j = KMAX / 2; j > 0; j >>= 1) {
-#pragma unroll
-    for (int i = 0; i < KMAX; ++i) {
-      if ((i & j) == 0) {
-        const float a = L[i], b = L[i + j];
-        L[i] = fminf(a, b);
-        L[i + j] = fmaxf(a, b);
-      }
-    }
+    const uint32_t x = L[net.a[c]], y = L[net.b[c]];
+    L[net.a[c]] = umin(x, y);
+    L[net.b[c]] = umax(x, y);
   }
 }
 
@@ -418,6 +451,10 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   IdxT *nbr = (IdxT *)M.nbr;
   constexpr bool kPacked = sizeof(IdxT) == 2;  // shared-memory path: bit-packed neighbour table
   const uint32_t nbB = nb_bits(M.cap), nbW = nb_words(M.cap, KMAX);
+  float *const X = M.X;
+  float *const Y = M.Y;
+  float *const Z = M.Z;
+  uint32_t *const W = M.W;
 
   // ---- Eq. 10-11: the leaf's box origin and voxel size h come from the prep kernel
   if (tid == 0) {
@@ -456,7 +493,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     if (i < nt) vslot[i] = sl;
   }
   __syncthreads();
-  // lookup, gate, compaction of P_1 (order preserved)
+  // lookup, gate, compaction of P_1 (order preserved) into the coordinate arrays
   const uint32_t fbeg = A.frames[lf.frame].begin;
   for (uint32_t base = 0; base < nt; base += NT) {
     const uint32_t i = base + tid;
@@ -489,23 +526,28 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     for (uint32_t ww = 0; ww < w; ++ww) off += S.wsum[ww];
     if (in1) {
       const uint32_t pos = off + __popc(bal & lt);
-      M.p1[pos] = p;  // in place for a shared-memory leaf: pos <= i, and this round's reads are done
+      X[pos] = p.x;
+      Y[pos] = p.y;
+      Z[pos] = p.z;
+      W[pos] = g;
     }
     __syncthreads();
     if (tid == 0) {
       uint32_t t = 0;
       for (uint32_t ww = 0; ww < NW; ++ww) t += S.wsum[ww];
       S.run += t;
-      if (base + NT >= nt)  // last round: the sentinels after P_1
-        for (uint32_t u = 0; u < kPad; ++u) M.p1[S.run + u] = make_float4(NAN, NAN, NAN, 0.0f);
-      if (base + NT >= nt)
-        for (int u = 1; u <= (int)kPadFront; ++u) M.p1[-u] = make_float4(NAN, NAN, NAN, 0.0f);
     }
     __syncthreads();
   }
   const uint32_t n1 = S.run;
+  for (uint32_t u = tid; u < kPad; u += NT) {  // the NaN padding after P_1
+    X[n1 + u] = __int_as_float(0x7FFFFFFF);
+    Y[n1 + u] = __int_as_float(0x7FFFFFFF);
+    Z[n1 + u] = __int_as_float(0x7FFFFFFF);
+    W[n1 + u] = 0u;
+  }
   if (n1 <= 1) {  // no neighbour exists: the density gate cannot keep it
-    for (uint32_t i = tid; i < n1; i += NT) write_point<kRec>(A, __float_as_uint(M.p1[i].w), 0, 0.0f, 2);
+    for (uint32_t i = tid; i < n1; i += NT) write_point<kRec>(A, W[i], 0, 0.0f, 2);
     return;
   }
   const uint32_t keff = (P.k < n1 - 1) ? P.k : n1 - 1;
@@ -519,112 +561,109 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     S.crank = (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;
   }
   const uint32_t sn = pow2ceil(n1);
+  __syncthreads();  // P_1 and its padding complete
 
-  // ---- kNN on P_1 (excluding self), order by (d^2, input index): one thread per query.
-  // Phase A finds theta, the k_eff-th smallest d^2, in a sorted register list of
-  // FP32 values (placeholders -1 fill the unused KMAX - k_eff slots).  The list
-  // is seeded with k_eff Morton-order neighbours of the query (window [ws, we])
-  // and sorted once by a register sorting network.  The scan then broadcasts the
-  // other candidates from shared memory to the warp, four per step (four
-  // independent distance chains); a lane whose candidate beats its current k-th
-  // value parks it in its column of a small shared buffer, and once some lane
-  // could overflow its slots at the next step the warp merges the parked values
-  // into the lists (sort of the slots + bitonic merge), so the list update is
-  // paid once per batch, not per insertion.
-  // Phase B rescans all candidates by chunks of 32: every d^2 < theta is kept;
-  // the candidates at exactly theta are counted and, when exactly as many ties
-  // as needed exist, all kept.  Otherwise (exact lattices, duplicates) extra
-  // scans take the ties in input-index order.  The set is the k_eff smallest by
-  // (d^2, input index), as with a full sort.
+  // ---- kNN on P_1 (excluding self), order (d^2, input index): one thread per query,
+  // candidates broadcast from shared memory to the warp, four per 16-byte load.
+  // The k_eff smallest are found by counting, not by keeping a sorted list
+  // (gd_knn_select.cuh): an upper bound theta_0 (the largest d^2 over a window
+  // of Morton neighbours holding k_eff others) fixes 32 buckets of a quarter
+  // octave below it; pass 1 counts every candidate into them (bit-sliced
+  // counters), which locates the boundary bucket B and the number of
+  // neighbours below it; pass 2 emits those neighbours in position order and
+  // parks B's few members, which are sorted to finish the set.  A boundary
+  // bucket with more members than the buffer is counted again at 32 times the
+  // resolution first.  Ties in d^2 across the cut are broken by input index.
   {
-    // parked candidates live in the sort buffer and wa, both idle during the kNN
-    // (pend_slots<KMAX>() columns of kLeafThreads)
-    float *const pend = reinterpret_cast<float *>(M.sbuf);
+    constexpr int PL = kPacked ? 11 : 21;  // count planes: counts < 2^PL (n1 - 1 candidates)
+    if (!kPacked && n1 >= (1u << PL)) {     // beyond the spill path's counters: refuse, do not guess
+      if (tid == 0) atomicOr(&A.ctr->status, kStInternal);
+      return;
+    }
+    uint32_t *const pend = M.pend;
     const float delta2 = __fmul_rn(S.delta, S.delta);
     const uint32_t cap = M.cap;
+    const uint32_t pbits = nbB;  // position bits of a parked key
+    const uint32_t pmask = (1u << pbits) - 1u;
+    const uint32_t n16 = (n1 + 15u) >> 4;
     const bool dbg_n = (kRec && A.use_dbg) && A.dbg.nbr, dbg_d = (kRec && A.use_dbg) && A.dbg.nbr_d2;
     for (uint32_t qb = 0; qb < n1; qb += NT) {
       const uint32_t q = qb + tid;
       const bool act = q < n1;
       if (!__any_sync(0xFFFFFFFFu, act)) continue;  // whole warp idle (warp-uniform)
       const uint32_t qq = act ? q : n1 - 1;          // idle lanes shadow a real query, results discarded
-      const float4 me = M.p1[qq];
-      const uint32_t j0 = qb + w * 32;               // < n1: lane 0 of a busy warp is busy
-      // Seed window [ws, we] (k_eff + 1 positions holding the query): with k_eff >= 32,
-      // or when it is the whole leaf, one window for the whole warp (it holds the
-      // warp's 32 queries), so that the scan needs no per-lane window test; otherwise
-      // centred on the lane's query.
-      const bool uni = keff >= 32u || keff + 1u == n1;  // a whole-leaf window serves the warp too
-      const uint32_t half = keff / 2;
-      uint32_t ws = uni ? j0 : ((qq > half) ? qq - half : 0u);
-      if (ws > n1 - 1 - keff) ws = n1 - 1 - keff;
-      const uint32_t we = ws + keff;
-      float L[KMAX];
-#pragma unroll
-      for (int sl = 0; sl < KMAX; ++sl) {
-        const int r = sl - (KMAX - (int)keff);
-        float v = -1.0f;
-        if (r >= 0) {
-          uint32_t j = ws + (uint32_t)r;
-          if (j >= qq) ++j;
-          v = sqdist(me, M.p1[j]);
-        }
-        L[sl] = v;
-      }
-      regsort_f<KMAX>(L);
-      uint32_t np = 0;
-      if (uni) {
-        // forward from we + 1 to n1 (the tail reads the sentinels after P_1), then
-        // backward from ws to 0 (the last step may read the sentinels before it)
-        const uint32_t s0 = (n1 - we + 2u) >> 2, ns = s0 + ((ws + 3u) >> 2);
-        for (uint32_t sI = 0; sI < ns; ++sI) {
-          const int j = (sI < s0) ? (int)(we + 1u + 4u * sI) : (int)ws - 4 * (int)(sI - s0 + 1u);
-          float dd[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) dd[u] = sqdist(me, M.p1[j + u]);
-          const float thr = L[KMAX - 1];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (dd[u] < thr) {
-              pend[np * kLeafThreads + tid] = dd[u];
-              ++np;
-            }
-          }
-          if (__any_sync(0xFFFFFFFFu, np + 4 > pend_slots<KMAX>() || sI + 1 == ns)) {
-            merge_pending<KMAX>(L, pend, np, tid);
-            np = 0;
-          }
-        }
-      } else {
-        // steps of 4 candidates: forward over [j0, n1 rounded up to 4) (the tail reads
-        // sentinels), then backward from j0 to 0; the last step also merges what is still parked
-        const uint32_t s0 = (n1 - j0 + 3u) >> 2, ns = s0 + (j0 >> 2);
-        const uint32_t wlen = we - ws;  // candidate j is a seed (or the query) iff j - ws <= wlen, unsigned
-        for (uint32_t sI = 0; sI < ns; ++sI) {
-          const uint32_t j = (sI < s0) ? j0 + 4u * sI : j0 - 4u * (sI - s0 + 1u);
-          float dd[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) dd[u] = sqdist(me, M.p1[j + u]);
-          const float thr = L[KMAX - 1];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (dd[u] < thr && j + u - ws > wlen) {
-              pend[np * kLeafThreads + tid] = dd[u];
-              ++np;
-            }
-          }
-          if (__any_sync(0xFFFFFFFFu, np + 4 > pend_slots<KMAX>() || sI + 1 == ns)) {
-            merge_pending<KMAX>(L, pend, np, tid);
-            np = 0;
-          }
+      const float xq = X[qq], yq = Y[qq], zq = Z[qq];
+      const uint32_t gq = W[qq];
+      const f32x2 QX = pk2(xq, xq), QY = pk2(yq, yq), QZ = pk2(zq, zq);
+      // theta_0: the largest d^2 over the window [w0, w0 + k_eff] of Morton
+      // neighbours (k_eff others at least), read in aligned steps of 4 (NaN padding ignored)
+      float t0 = 0.0f;
+      {
+        uint32_t w0 = (qq > keff / 2) ? qq - keff / 2 : 0u;
+        if (w0 > n1 - 1 - keff) w0 = n1 - 1 - keff;
+        const uint32_t wa0 = w0 & ~3u, wsteps = (keff + 7u) >> 2;
+        for (uint32_t s = 0; s < wsteps; ++s) {
+          float d[4];
+          sqdist4(X, Y, Z, wa0 + 4u * s, QX, QY, QZ, d);
+          t0 = fmaxf(fmaxf(t0, d[0]), fmaxf(fmaxf(d[1], d[2]), d[3]));
         }
       }
-      const float theta = L[KMAX - 1];
-      uint32_t below = 0;
+      SelLevel L{__float_as_int(t0), -1, kSelS0, 0u};
+      SelCut cut;
+      {
+        // pass 1: every candidate (and the query itself, taken out in the walk) into the buckets
+        uint32_t c[PL];
 #pragma unroll
-      for (int sl = 0; sl < KMAX; ++sl) below += (L[sl] >= 0.0f && L[sl] < theta) ? 1u : 0u;
-      const uint32_t ties_needed = keff - below;  // >= 1: theta itself is a candidate
-      const uint32_t gq = __float_as_uint(me.w);
+        for (int p = 0; p < PL; ++p) c[p] = 0u;
+#pragma unroll 1
+        for (uint32_t s = 0; s < n16; ++s) {
+          uint32_t m[16];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            float d[4];
+            sqdist4(X, Y, Z, 16u * s + 4u * u, QX, QY, QZ, d);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) m[4 * u + v] = sel_bucket_bit(L.tb, __float_as_int(d[v]), L.S);
+          }
+          sel_add16<PL>(c, m);
+        }
+        cut = sel_walk<PL>(c, L, keff);
+        // refinements: count again inside the boundary bucket where it is too full
+        // for the buffer (or too wide for a packed key); lanes that are done
+        // repeat their own level and get the same result
+#pragma unroll 1
+        for (int level = 1;; ++level) {
+          const bool single = cut.hi == cut.lo + 1;  // one d^2 value: exact ties, resolved below
+          const bool again = act && !single && (cut.c_at > kSelBuf || !sel_fits(cut, pbits));
+          if (!__any_sync(0xFFFFFFFFu, again)) break;
+          if (level > kSelMaxLevels) {  // cannot happen: the range shrinks at every level
+            atomicOr(&A.ctr->status, kStInternal);
+            break;
+          }
+          if (again) L = sel_refine(L, cut);
+#pragma unroll
+          for (int p = 0; p < PL; ++p) c[p] = 0u;
+#pragma unroll 1
+          for (uint32_t s = 0; s < n16; ++s) {
+            uint32_t m[16];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              float d[4];
+              sqdist4(X, Y, Z, 16u * s + 4u * u, QX, QY, QZ, d);
+#pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                const int32_t db = __float_as_int(d[v]);
+                m[4 * u + v] = (db > L.lo) ? sel_bucket_bit(L.tb, db, L.S) : 0u;
+              }
+            }
+            sel_add16<PL>(c, m);
+          }
+          cut = sel_walk<PL>(c, L, keff);
+        }
+      }
+      const uint32_t need = keff - cut.c_below;     // 1 <= need <= c_at
+      const bool ties_only = cut.c_at > kSelBuf;    // a single d^2 value with more members than the buffer
+      const int32_t kbase = cut.lo + 1;              // smallest bits of bucket B's range
       // Record neighbour t of this query (position npos, input index g, distance d2).
       // Ranks come in order t = 0, 1, ...: the packed table is filled through a
       // bit buffer, one word store per 32 bits.
@@ -652,82 +691,119 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           }
         }
       };
-      // every d^2 < theta is a neighbour; the ntie candidates at exactly theta are
-      // counted and the position of the last one kept (common case: one tie, the
-      // k_eff-th neighbour itself).  The scan goes by chunks of 32 candidates: two
-      // bit masks (d^2 < theta, d^2 <= theta) per chunk, then the neighbours of the
-      // chunk are emitted from the first mask in position order.
-      uint32_t a = 0, ntie = 0, tp = 0;
+      // pass 2, by chunks of 32 candidates: two bit masks (d^2 <= bottom of B's
+      // range: a neighbour; d^2 <= top of B's range: B or below).  The
+      // comparisons go through the FMA pipe: for IEEE subtraction (no flush to
+      // zero) the sign bit of v - d^2 is set exactly when d^2 > v; a funnel shift
+      // appends each sign bit, so the chunk's first candidate ends in bit 31.
+      const float lo_f = cut.lo >= 0 ? __int_as_float(cut.lo) : -1.0f;
+      const float hi_f = __int_as_float(cut.hi);
+      const f32x2 LO2 = pk2(lo_f, lo_f), HI2 = pk2(hi_f, hi_f);
+      uint32_t a = 0, np = 0;
+#pragma unroll 1
       for (uint32_t c0 = 0; c0 < n1; c0 += 32u) {
-        // The comparisons go through the FMA pipe: for IEEE subtraction (no flush to
-        // zero) x - y is negative exactly when x < y, so the sign bit of d^2 - theta is
-        // (d^2 < theta) and that of theta - d^2 is !(d^2 <= theta) (NaN gives sign 0).
-        // A funnel shift appends each sign bit: the chunk's first candidate ends in bit 31.
-        uint32_t lt = 0, gt = 0;
+        uint32_t gtlo = 0, gthi = 0;
 #pragma unroll 2
         for (uint32_t st = 0; st < 8; ++st) {
-          float dv[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) dv[u] = sqdist(me, M.p1[c0 + st * 4 + u]);
+          float d[4];
+          sqdist4(X, Y, Z, c0 + 4u * st, QX, QY, QZ, d);
+          const f32x2 D0 = pk2(d[0], d[1]), D1 = pk2(d[2], d[3]);
+          float e[4], f[4];
+          upk2(sub2(LO2, D0), e[0], e[1]);
+          upk2(sub2(LO2, D1), e[2], e[3]);
+          upk2(sub2(HI2, D0), f[0], f[1]);
+          upk2(sub2(HI2, D1), f[2], f[3]);
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            lt = __funnelshift_l(__float_as_uint(__fsub_rn(dv[u], theta)), lt, 1);
-            gt = __funnelshift_l(__float_as_uint(__fsub_rn(theta, dv[u])), gt, 1);
+            gtlo = __funnelshift_l(__float_as_uint(e[u]), gtlo, 1);
+            gthi = __funnelshift_l(__float_as_uint(f[u]), gthi, 1);
           }
         }
-        lt = __brev(lt);
-        uint32_t le = __brev(~gt);
-        // the query itself is no candidate; positions past n1 (NaN sentinels) are
-        // outside d^2 < theta already and are masked out of d^2 <= theta
+        const uint32_t le_lo = ~__brev(gtlo), le_hi = ~__brev(gthi);
+        // the query itself is no candidate; positions past n1 (NaN padding) are dropped
         uint32_t keep = (qq - c0 < 32u) ? ~(1u << (qq - c0)) : 0xFFFFFFFFu;
         if (n1 - c0 < 32u) keep &= (1u << (n1 - c0)) - 1u;
-        lt &= keep;
-        le &= keep;
-        const uint32_t tie = le & ~lt;
-        if (tie) {
-          ntie += __popc(tie);
-          tp = c0 + 31u - __clz(tie);
-        }
-        while (lt) {
-          const uint32_t ju = c0 + (uint32_t)(__ffs(lt) - 1);
-          lt &= lt - 1u;
-          if (act && a < keff) {
-            const float4 cj = M.p1[ju];
-            emit(a, ju, __float_as_uint(cj.w), sqdist(me, cj));
-          }
+        uint32_t em = le_lo & keep;
+        uint32_t pm = le_hi & ~le_lo & keep;
+        while (em) {
+          const uint32_t ju = c0 + (uint32_t)(__ffs(em) - 1);
+          em &= em - 1u;
+          if (act && a < keff) emit(a, ju, W[ju], (kRec ? sqdist(xq, yq, zq, X[ju], Y[ju], Z[ju]) : 0.0f));
           ++a;
         }
+        while (pm) {
+          const uint32_t ju = c0 + (uint32_t)(__ffs(pm) - 1);
+          pm &= pm - 1u;
+          if (act && !ties_only && np < kSelBuf) {
+            const int32_t db = __float_as_int(sqdist(xq, yq, zq, X[ju], Y[ju], Z[ju]));
+            pend[np * kLeafThreads + tid] = ((uint32_t)(db - kbase) << pbits) | ju;
+          }
+          ++np;
+        }
       }
-      if (act && a != below) atomicOr(&A.ctr->status, kStInternal);  // the two phases must agree
-      // ties: with exactly ties_needed of them all are taken, otherwise the
-      // ties_needed smallest input indices (rare: exact lattices, duplicates)
-      const bool all_ties = ntie == ties_needed;
-      if (act && all_ties && ties_needed == 1) emit(below, tp, __float_as_uint(M.p1[tp].w), theta);
-      // one scan emits every tie; or one scan per tie picks the smallest index above the last
-      const uint32_t rounds = !act ? 0u : all_ties ? (ties_needed > 1 ? 1u : 0u) : ties_needed;
+      if (act && (a != cut.c_below || np != cut.c_at)) atomicOr(&A.ctr->status, kStInternal);  // passes agree
+      // the need smallest of bucket B: sort the parked keys ((d^2 offset, position));
+      // d^2 ties straddling the cut are ranked by input index
+      float theta = hi_f;
+      const bool parked = act && !ties_only;
+      uint32_t K[kSelBuf];
+#pragma unroll
+      for (int i = 0; i < (int)kSelBuf; ++i) K[i] = (parked && (uint32_t)i < np) ? pend[i * kLeafThreads + tid] : 0xFFFFFFFFu;
+      regsort_u<kSelBuf>(K);
+      uint32_t th_off = 0, n_lt = 0, n_eq = 0;
+#pragma unroll
+      for (int i = 0; i < (int)kSelBuf; ++i)
+        if ((uint32_t)i + 1u == need) th_off = K[i] >> pbits;
+#pragma unroll
+      for (int i = 0; i < (int)kSelBuf; ++i) {
+        if ((uint32_t)i < np) {
+          n_lt += (K[i] >> pbits) < th_off;
+          n_eq += (K[i] >> pbits) == th_off;
+        }
+      }
+      const uint32_t need_eq = need - n_lt;            // of the n_eq keys at the cut distance
+      const bool straddle = parked && n_eq > need_eq;  // rank those by input index
+      if (parked) theta = __int_as_float(kbase + (int32_t)th_off);
+#pragma unroll
+      for (int i = 0; i < (int)kSelBuf; ++i) {
+        const uint32_t off = K[i] >> pbits, ju = K[i] & pmask;
+        bool take = parked && (uint32_t)i < need;
+        if (straddle && (uint32_t)i < np && off == th_off) {
+          const uint32_t gi = W[ju];
+          uint32_t before = 0;
+#pragma unroll
+          for (int j = 0; j < (int)kSelBuf; ++j) {
+            if ((uint32_t)j < np && (K[j] >> pbits) == th_off) before += W[K[j] & pmask] < gi;
+          }
+          take = before < need_eq;
+        }
+        if (take) emit(a++, ju, W[ju], __int_as_float(kbase + (int32_t)off));
+      }
+      // exact ties beyond the buffer (lattices, duplicates): one scan per missing
+      // neighbour takes the smallest input index above the last one taken
+      const uint32_t rounds = (act && ties_only) ? need : 0u;
       const uint32_t max_rounds = __reduce_max_sync(0xFFFFFFFFu, rounds);
-      uint32_t last = 0, slot = below;
+      uint32_t last = 0;
+#pragma unroll 1
       for (uint32_t r = 0; r < max_rounds; ++r) {
         uint32_t bg = 0xFFFFFFFFu, bp = 0;
+#pragma unroll 1
         for (uint32_t j = 0; j < n1; ++j) {
-          const float4 cj = M.p1[j];
-          const float d2 = sqdist(me, cj);
-          if (r >= rounds || j == qq || d2 != theta) continue;
-          const uint32_t g = __float_as_uint(cj.w);
-          if (all_ties) {
-            if (slot < keff) emit(slot++, j, g, theta);
-          } else if ((r == 0 || g > last) && g < bg) {
+          const float d2 = sqdist(xq, yq, zq, X[j], Y[j], Z[j]);
+          const uint32_t g = W[j];
+          if (r < rounds && j != qq && d2 == hi_f && (r == 0 || g > last) && g < bg) {
             bg = g;
             bp = j;
           }
         }
-        if (r < rounds && !all_ties && slot < keff) {
-          emit(slot++, bp, bg, theta);
+        if (r < rounds) {
+          emit(a++, bp, bg, hi_f);
           last = bg;
         }
       }
       if (kPacked && act && nb_n > 0) nbw[nb_w] = (uint32_t)nb_acc;  // last partial word
       if (act) {
+        if (a != keff) atomicOr(&A.ctr->status, kStInternal);
         const float rt = (theta < delta2) ? delta2 : theta;
         M.r2[qq] = rt;
         if (kRec && (A.use_dbg || A.use_train) && rec_index_ok(A, gq)) {
@@ -794,7 +870,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       const float ell = __fsub_rn(Lref, __fmul_rn(1.5f, log2f(__fdiv_rn(r2, r2ref))));  // log2(rho_i / sqrt(rho_med^2 + eps))
       M.wa[i] = __fmul_rn(half_alpha, ell);
       if (kRec && A.use_train) {
-        const uint32_t g = __float_as_uint(M.p1[i].w);
+        const uint32_t g = W[i];
         if (rec_index_ok(A, g)) A.train.ell[g] = ell;
       }
     }
@@ -809,7 +885,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     const float hg = 0.5f * P.gamma, ek = P.eps_k;
     for (uint32_t i = tid; i < n1; i += NT) {
       if (!M.flag[i]) continue;
-      const float4 me = M.p1[i];
+      const float xi = X[i], yi = Y[i], zi = Z[i];
       const float ai = M.wa[i], ci = __fdiv_rn(c2, M.r2[i]);  // r2_i's last read: F_i takes its place
       // two neighbours per step into two partial sums (independent chains),
       // F = even-rank terms + odd-rank terms
@@ -833,7 +909,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         }
       };
       auto term = [&](uint32_t j) {
-        const float d2 = sqdist(me, M.p1[j]);
+        const float d2 = sqdist(xi, yi, zi, X[j], Y[j], Z[j]);
         const float wt = ex2_hw(__fmaf_rn(-d2, ci, __fadd_rn(ai, M.wa[j])));  // w_den * w_dis (Eq. 17, 19)
         const float D = g2 ? d2 : pow_half_gamma(d2, hg);                    // (d^2)^(gamma/2)
         return __fmul_rn(wt, rcp_hw(__fadd_rn(D, ek)));                    // kernel of Eq. 20
@@ -890,11 +966,11 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         if (needed >= tied) {
           keep = true;
         } else {  // exact score ties at the cut: rank the tied points by input index
-          const uint32_t g = __float_as_uint(M.p1[i].w);
+          const uint32_t g = W[i];
           uint32_t before = 0;
           for (uint32_t j2 = 0; j2 < n1; ++j2)
             before += (M.flag[j2] && 0xFFFFFFFFu - __float_as_uint(M.F[j2]) == cut &&
-                       __float_as_uint(M.p1[j2].w) < g);
+                       W[j2] < g);
           keep = before < needed;
         }
       }
@@ -908,7 +984,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   // ---- Eq. 22: results in input order
   const double rho_med = S.rho_med;
   for (uint32_t i = tid; i < n1; i += NT) {
-    const uint32_t g = __float_as_uint(M.p1[i].w);
+    const uint32_t g = W[i];
     const uint8_t f = M.flag[i];
     if (f == 0) write_point<kRec>(A, g, 0, 0.0f, 2);
     else write_point<kRec>(A, g, f == 2, M.F[i], f == 2 ? 0 : 3);
@@ -932,12 +1008,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, uint32_t
   return false;
 }
 
-// 6 CTAs of 128 threads per SM by registers (at most 85 per thread) for K <= 32
-// (a 512-point, K = 32 leaf takes 35 KB of shared memory, so 6 fit there too);
-// the K = 64 lists need more.  kRec: the debug / training outputs are written
-// (a separate instantiation, so that the plain path carries none of their code).
+// 5 CTAs of 128 threads per SM for K <= 32 (a 512-point, K = 32 leaf takes 39 KB
+// of shared memory, and at most 102 registers a thread fit 5 CTAs); the K = 64
+// tables need more shared memory.  kRec: the debug / training outputs are
+// written (a separate instantiation, so that the plain path carries none of
+// their code).
 template <int KMAX, bool kRec>
-__global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 6) k_leaf(const LeafArgs A) {
+__global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 5) k_leaf(const LeafArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long s_mbar;
   __shared__ LeafShared S;
@@ -945,7 +1022,7 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 6) k_leaf(con
   const uint32_t lmax = A.lmax;
   LeafMem Ms;
   carve<uint16_t>(smem, lmax, KMAX, &Ms);
-  float4 *const s_pts = Ms.p1;  // the raw points land in p1 (compacted in place)
+  float4 *const s_pts = Ms.raw;  // the raw points land here, P_1 is compacted out of them
   const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -983,6 +1060,7 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 6) k_leaf(con
     } else {
       LeafMem Mg;
       carve<uint32_t>(A.big_scratch + (size_t)lf.start * A.big_bpp, lf.count, KMAX, &Mg);
+      Mg.pend = Ms.pend;  // the per-query parked keys live in shared memory on this path too
       process_leaf<KMAX, uint32_t, kRec>(A, lf, A.spts + lf.start, Mg, S);
     }
     __syncthreads();

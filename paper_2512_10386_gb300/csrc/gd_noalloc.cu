@@ -23,7 +23,7 @@ namespace {
 constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kN = DENOISE_NOALLOC_MAX_POINTS;
 constexpr size_t kTiles = (kN + kTilePts - 1) / kTilePts;
-constexpr uint32_t kSpillBpp = 384;  // leaf_big_bpp(64): checked against the library at first use
+constexpr uint32_t kSpillBpp = 320;  // leaf_big_bpp(64): checked against the library at first use
 // carve of the scratch array
 constexpr size_t kOffKeys0 = 0;
 constexpr size_t kOffKeys1 = kOffKeys0 + al256(8 * kN);
