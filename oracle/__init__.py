@@ -110,6 +110,12 @@ def _load():
         lib.orc_cbrt_spec.restype = ctypes.c_double
         lib.orc_interleave.argtypes = [ctypes.c_uint32] * 3
         lib.orc_interleave.restype = ctypes.c_uint64
+        lib.orc_nn_d2.argtypes = [_P, ctypes.c_int64, _P, ctypes.c_int64, _P]
+        lib.orc_nn_d2.restype = ctypes.c_int
+        lib.orc_metrics.argtypes = [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P]
+        lib.orc_metrics.restype = ctypes.c_int
+        lib.orc_baseline.argtypes = [_P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _P, _P, _P, _P, _P, _P]
+        lib.orc_baseline.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -184,3 +190,50 @@ def cbrt_spec(u: float) -> float:
 
 def interleave(qx: int, qy: int, qz: int) -> int:
     return int(_load().orc_interleave(qx, qy, qz))
+
+
+def _xyz(a):
+    return np.ascontiguousarray(a, dtype=np.float32).reshape(-1, 3)
+
+
+def nn_d2(a, b) -> np.ndarray:
+    """Squared distance from each point of ``a`` to its nearest point of ``b`` (FP64, brute force)."""
+    a, b = _xyz(a), _xyz(b)
+    out = np.zeros(max(len(a), 1), np.float64)
+    st = _load().orc_nn_d2(_ptr(a), len(a), _ptr(b), len(b), _ptr(out))
+    if st != OK:
+        raise OracleError(st)
+    return out[:len(a)]
+
+
+def metrics(clean, denoised) -> dict:
+    """MSE and PSNR of Eq. 29 (nearest-neighbour correspondence, M = the clean
+    cloud's bounding-box diagonal) and the Chamfer distance of Eq. 30."""
+    a, b = _xyz(clean), _xyz(denoised)
+    v = np.zeros(3, np.float64)
+    st = _load().orc_metrics(_ptr(a), len(a), _ptr(b), len(b), _ptr(v[0:]), v[1:].ctypes.data,
+                             v[2:].ctypes.data)
+    if st != OK:
+        raise OracleError(st)
+    return {"mse": float(v[0]), "chamfer": float(v[1]), "psnr": float(v[2])}
+
+
+G_DEFAULT = 6.67e-11   # Eq. 6: the gravitational constant as the paper sets it
+ALPHA_DEFAULT = 600.0  # Eq. 7: the paper's weighting parameter
+
+
+def baseline(xyz, G: float = G_DEFAULT, alpha: float = ALPHA_DEFAULT) -> dict:
+    """The gravitational-function baseline of Sec. 2.2 (Eq. 1-9)."""
+    xyz = _xyz(xyz)
+    n = len(xyz)
+    nn = max(n, 1)
+    r = {"keep": np.zeros(nn, np.uint8), "n_i": np.zeros(nn, np.uint32), "d_i": np.zeros(nn, np.float64),
+         "F_i": np.zeros(nn, np.float64)}
+    RT = np.zeros(2, np.float64)
+    st = _load().orc_baseline(_ptr(xyz), n, G, alpha, _ptr(r["keep"]), _ptr(r["n_i"]), _ptr(r["d_i"]),
+                              _ptr(r["F_i"]), RT[0:].ctypes.data, RT[1:].ctypes.data)
+    if st != OK:
+        raise OracleError(st)
+    out = {k: v[:n] for k, v in r.items()}
+    out["R"], out["T"] = float(RT[0]), float(RT[1])
+    return out

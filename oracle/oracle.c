@@ -512,3 +512,109 @@ int orc_softf1(const float *xyz, int64_t n, const orc_params *p, const uint8_t *
   free(F); free(dF); free(rm); free(dm); free(stg);
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Eq. 29-30: nearest-neighbour distances, Chamfer distance and PSNR    */
+/* ------------------------------------------------------------------ */
+int orc_nn_d2(const float *a, int64_t na, const float *b, int64_t nb, double *out) {
+  if (na < 0 || nb <= 0 || !out) return ORC_EINVAL;
+  for (int64_t i = 0; i < na; ++i) {
+    double best = INFINITY;
+    for (int64_t j = 0; j < nb; ++j) {
+      double d2 = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        double t = (double)a[3 * i + c] - (double)b[3 * j + c];
+        d2 += t * t;
+      }
+      if (d2 < best) best = d2;
+    }
+    out[i] = best;
+  }
+  return ORC_OK;
+}
+
+int orc_metrics(const float *clean, int64_t na, const float *den, int64_t nb, double *mse, double *cd,
+                double *psnr) {
+  if (na <= 0 || nb <= 0) return ORC_EINVAL;
+  double *da = (double *)malloc(sizeof(double) * (size_t)na);
+  double *db = (double *)malloc(sizeof(double) * (size_t)nb);
+  if (!da || !db) return ORC_ENOMEM;
+  orc_nn_d2(clean, na, den, nb, da);
+  orc_nn_d2(den, nb, clean, na, db);
+  double sa = 0.0, sb = 0.0;
+  for (int64_t i = 0; i < na; ++i) sa += da[i];
+  for (int64_t j = 0; j < nb; ++j) sb += db[j];
+  const double m = sa / (double)na;
+  double lo[3], hi[3];
+  for (int c = 0; c < 3; ++c) lo[c] = hi[c] = clean[c];
+  for (int64_t i = 1; i < na; ++i)
+    for (int c = 0; c < 3; ++c) {
+      if (clean[3 * i + c] < lo[c]) lo[c] = clean[3 * i + c];
+      if (clean[3 * i + c] > hi[c]) hi[c] = clean[3 * i + c];
+    }
+  double M2 = 0.0;
+  for (int c = 0; c < 3; ++c) M2 += (hi[c] - lo[c]) * (hi[c] - lo[c]);
+  if (mse) *mse = m;
+  if (cd) *cd = m + sb / (double)nb;
+  if (psnr) *psnr = 10.0 * log10(M2 / m);
+  free(da);
+  free(db);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.2, Eq. 1-9: the gravitational-function baseline               */
+/* ------------------------------------------------------------------ */
+int orc_baseline(const float *xyz, int64_t n, double G, double alpha, uint8_t *keep, uint32_t *n_i,
+                 double *d_i, double *F_i, double *R_out, double *T_out) {
+  if (n <= 0 || !keep) return ORC_EINVAL;
+  for (int64_t i = 0; i < 3 * n; ++i)
+    if (!isfinite(xyz[i])) return ORC_ENONFINITE;
+  /* Eq. 1: centroid */
+  double theta[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = 0; i < n; ++i)
+    for (int c = 0; c < 3; ++c) theta[c] += (double)xyz[3 * i + c];
+  for (int c = 0; c < 3; ++c) theta[c] /= (double)n;
+  /* Eq. 2: extents */
+  double H[3];
+  for (int c = 0; c < 3; ++c) {
+    float lo = xyz[c], hi = xyz[c];
+    for (int64_t i = 1; i < n; ++i) {
+      if (xyz[3 * i + c] < lo) lo = xyz[3 * i + c];
+      if (xyz[3 * i + c] > hi) hi = xyz[3 * i + c];
+    }
+    H[c] = (double)hi - (double)lo;
+  }
+  /* Eq. 3: neighbourhood radius; Eq. 7: threshold */
+  const double R = 6.0 * (H[0] * H[1] + H[0] * H[2] + H[1] * H[2]) / (double)n;
+  const double T = alpha * G * (H[0] + H[1] + H[2]) / (double)n;
+  const double R2 = R * R;
+  if (R_out) *R_out = R;
+  if (T_out) *T_out = T;
+  for (int64_t i = 0; i < n; ++i) {
+    /* Eq. 4 */
+    double dd = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      double t = (double)xyz[3 * i + c] - theta[c];
+      dd += t * t;
+    }
+    const double d = sqrt(dd);
+    /* Eq. 5: every point within R, the point itself included */
+    uint32_t cnt = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      float dx = xyz[3 * j] - xyz[3 * i];
+      float dy = xyz[3 * j + 1] - xyz[3 * i + 1];
+      float dz = xyz[3 * j + 2] - xyz[3 * i + 2];
+      float xx = dx * dx;
+      float d2 = fmaf(dz, dz, fmaf(dy, dy, xx));
+      cnt += ((double)d2 <= R2);
+    }
+    /* Eq. 6 and Eq. 8 */
+    const double F = G * (double)cnt / (d * d);
+    keep[i] = F >= T / d;
+    if (n_i) n_i[i] = cnt;
+    if (d_i) d_i[i] = d;
+    if (F_i) F_i[i] = F;
+  }
+  return ORC_OK;
+}

@@ -76,6 +76,28 @@ int orc_denoise(const float *xyz, int64_t n, const orc_params *p, orc_out *out);
 int orc_softf1(const float *xyz, int64_t n, const orc_params *p, const uint8_t *noise,
                const uint8_t *in_loss, double *loss, double grad[4], double *removal);
 
+/* Evaluation metrics (Sec. 4.1, Eq. 29-30), FP64, brute force.
+ * orc_nn_d2: out[i] = min over j of ||a_i - b_j||^2.
+ * orc_metrics: with A = the clean cloud and B = the denoised cloud,
+ *   mse = mean over A of the squared distance to the nearest point of B
+ *         (the "corresponding point" of Eq. 29 is that nearest neighbour),
+ *   cd  = Eq. 30: mse + mean over B of the squared distance to the nearest point of A,
+ *   psnr = 10 log10(M^2 / mse), M = diagonal of A's bounding box.
+ * Both sets must be non-empty (ORC_EINVAL otherwise). */
+int orc_nn_d2(const float *a, int64_t na, const float *b, int64_t nb, double *out);
+int orc_metrics(const float *clean, int64_t na, const float *den, int64_t nb, double *mse, double *cd,
+                double *psnr);
+
+/* The gravitational-function baseline of Sec. 2.2 (Eq. 1-9).
+ *   centroid theta (Eq. 1), extents H (Eq. 2), radius R = 6(HxHy + HxHz + HyHz)/N (Eq. 3),
+ *   d_i = ||p_i - theta|| (Eq. 4), n_i = |{p_j : ||p_j - p_i|| <= R}| with p_i itself
+ *   counted (Eq. 5), F_i = G n_i / d_i^2 (Eq. 6), T = alpha G (Hx + Hy + Hz) / N (Eq. 7),
+ *   keep iff F_i >= T / d_i (Eq. 8-9).
+ * The neighbour test compares the FP32 squared distance (the method's fixed
+ * operation order) with R^2 in FP64.  Every output pointer may be NULL except keep. */
+int orc_baseline(const float *xyz, int64_t n, double G, double alpha, uint8_t *keep, uint32_t *n_i,
+                 double *d_i, double *F_i, double *R_out, double *T_out);
+
 /* Cube root used for Eq. 11: fixed Newton sequence in FP64 (see oracle.c). */
 double orc_cbrt_spec(double u);
 

@@ -47,6 +47,14 @@ MUTATIONS = [
      ("double z = (log(F[i]) - tau) / T;", "double dr_dF = -dm[i] / F[i];"),
      ("double z = (F[i] - tau) / T;", "double dr_dF = -dm[i];")),
     ("soft removal sign of tau", "double z = (log(F[i]) - tau) / T;", "double z = (log(F[i]) + tau) / T;"),
+    ("Chamfer second term dropped", "if (cd) *cd = m + sb / (double)nb;", "if (cd) *cd = m;"),
+    ("PSNR with M not M^2", "if (psnr) *psnr = 10.0 * log10(M2 / m);", "if (psnr) *psnr = 10.0 * log10(sqrt(M2) / m);"),
+    ("MSE over the denoised cloud", "const double m = sa / (double)na;", "const double m = sb / (double)nb;"),
+    ("baseline radius factor 6 -> 3", "const double R = 6.0 * (H[0] * H[1]", "const double R = 3.0 * (H[0] * H[1]"),
+    ("baseline self not counted", "cnt += ((double)d2 <= R2);", "cnt += ((double)d2 <= R2) && j != i;"),
+    ("baseline Eq. 8 with d^2", "keep[i] = F >= T / d;", "keep[i] = F >= T / (d * d);"),
+    ("baseline centroid over N-1", "for (int c = 0; c < 3; ++c) theta[c] /= (double)n;",
+     "for (int c = 0; c < 3; ++c) theta[c] /= (double)(n - 1);"),
     ("voxel origin shifted", "float d = coord(c, idx[t], a) - lo[a];", "float d = coord(c, idx[t], a) - lo[a] + h * 0.5f;"),
 ]
 

@@ -592,3 +592,101 @@ def test_f1_metric_definitions_bruteforce():
     keep = np.array([0, 0, 0, 1, 0, 0, 1, 1, 1, 1], bool)
     P, R, F1 = precision_recall_f1(keep, noise)
     assert (P, R) == (3 / 5, 3 / 4) and abs(F1 - 2 / 3) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# evaluation metrics (Sec. 4.1, Eq. 29-30)
+# --------------------------------------------------------------------------
+def test_nn_distances_match_kdtree(orc):
+    spatial = pytest.importorskip("scipy.spatial")
+    rng = np.random.default_rng(31)
+    a = rng.normal(size=(700, 3)).astype(np.float32)
+    b = (rng.normal(size=(500, 3)) * 1.3 + 0.2).astype(np.float32)
+    got = orc.nn_d2(a, b)
+    d, _ = spatial.cKDTree(b.astype(np.float64)).query(a.astype(np.float64), k=1)
+    assert np.allclose(got, d ** 2, rtol=1e-12, atol=0)
+
+
+def test_metrics_hand_worked(orc):
+    # A = {(0,0,0), (1,0,0)}, B = {(0,0,0)}: A->B squared distances 0 and 1 (mean 0.5),
+    # B->A 0; CD = 0.5; M = bbox diagonal of A = 1, PSNR = 10 log10(1 / 0.5)
+    a = np.array([[0, 0, 0], [1, 0, 0]], np.float32)
+    b = np.array([[0, 0, 0]], np.float32)
+    m = orc.metrics(a, b)
+    assert m["mse"] == 0.5 and m["chamfer"] == 0.5
+    assert abs(m["psnr"] - 10 * np.log10(2.0)) < 1e-12
+    # the Chamfer distance is symmetric; the MSE is not (it averages over the clean cloud)
+    m2 = orc.metrics(b, a)
+    assert m2["chamfer"] == 0.5 and m2["mse"] == 0.0
+
+
+def test_metrics_translated_lattice_closed_form(orc):
+    # a lattice of spacing 1 and a copy shifted by t (|t| < 1/2): each point's nearest
+    # neighbour is its own shifted copy, so MSE = |t|^2, CD = 2|t|^2 and
+    # PSNR = 10 log10(diag^2 / |t|^2) with diag^2 = 3 * 9^2 for a 10 x 10 x 10 lattice
+    g = np.arange(10, dtype=np.float32)
+    a = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    t = np.array([0.125, -0.25, 0.0625], np.float32)     # exact in FP32
+    b = a + t
+    t2 = float((t.astype(np.float64) ** 2).sum())
+    m = orc.metrics(a, b)
+    assert abs(m["mse"] - t2) < 1e-15 and abs(m["chamfer"] - 2 * t2) < 1e-15
+    assert abs(m["psnr"] - 10 * np.log10(3 * 81 / t2)) < 1e-9
+    same = orc.metrics(a, a)
+    assert same["chamfer"] == 0.0 and np.isinf(same["psnr"])
+
+
+# --------------------------------------------------------------------------
+# the gravitational-function baseline (Sec. 2.2, Eq. 1-9)
+# --------------------------------------------------------------------------
+def test_baseline_hand_worked_lattice(orc):
+    # 3 x 3 x 3 lattice, spacing 1: centroid = centre point, H = (2, 2, 2),
+    # R = 6 (4 + 4 + 4) / 27 = 8/3 (Eq. 3), T = 600 G 6 / 27 (Eq. 7).  Keep iff
+    # G n / d^2 >= T / d, i.e. n >= (600 * 6 / 27) d = 133.3 d: only the centre
+    # (d = 0, F infinite) survives, since n <= 27.
+    g = np.arange(3, dtype=np.float32)
+    xyz = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    r = orc.baseline(xyz)
+    assert abs(r["R"] - 8.0 / 3.0) < 1e-15
+    assert abs(r["T"] - 600 * 6.67e-11 * 6 / 27) < 1e-24
+    centre = int(np.where((xyz == 1).all(1))[0][0])
+    assert r["keep"][centre] == 1 and r["keep"].sum() == 1
+    # n_i: lattice points within 8/3 of each point (the point itself included), counted by hand
+    # per offset class: |dx|,|dy|,|dz| in {0,1,2} with dx^2+dy^2+dz^2 <= 64/9 (7.1): all but
+    # offsets with two or more 2s (8, 12) -> the centre sees all 27, a corner sees 27 - 7 = 20
+    corner = int(np.where((xyz == 0).all(1))[0][0])
+    assert r["n_i"][centre] == 27 and r["n_i"][corner] == 20
+    assert r["d_i"][corner] == np.sqrt(3.0)
+
+
+def test_baseline_counts_match_kdtree_and_threshold_rule(orc):
+    spatial = pytest.importorskip("scipy.spatial")
+    # a dense Gaussian cluster in sparse uniform noise, at a scale where Eq. 3's
+    # radius (not scale-free: an area over a count) separates the two
+    rng = np.random.default_rng(21)
+    xyz = np.concatenate([rng.normal(size=(3000, 3)) * 2.0, rng.uniform(-8, 8, size=(300, 3))]).astype(np.float32)
+    r = orc.baseline(xyz)
+    tree = spatial.cKDTree(xyz.astype(np.float64))
+    want = np.array([len(v) for v in tree.query_ball_point(xyz.astype(np.float64), r=r["R"])])
+    assert np.array_equal(r["n_i"], want)
+    theta = xyz.astype(np.float64).mean(0)
+    assert np.allclose(r["d_i"], np.linalg.norm(xyz - theta, axis=1), rtol=1e-12)
+    H = xyz.max(0).astype(np.float64) - xyz.min(0).astype(np.float64)
+    assert abs(r["R"] - 6 * (H[0] * H[1] + H[0] * H[2] + H[1] * H[2]) / len(xyz)) <= 1e-12 * r["R"]
+    # Eq. 8 with G cancelled: keep iff n_i >= alpha (Hx + Hy + Hz) d_i / N
+    rhs = 600.0 * H.sum() * r["d_i"] / len(xyz)
+    clear = np.abs(r["n_i"] - rhs) > 1e-6 * rhs
+    assert np.array_equal(r["keep"][clear].astype(bool), (r["n_i"] >= rhs)[clear])
+    assert r["keep"][:3000].mean() > 0.5 and r["keep"][3000:].mean() < 0.1   # cluster kept, noise removed
+
+
+def test_baseline_translation_and_permutation_invariance(orc):
+    from synth import object_cloud
+    xyz, _ = object_cloud(seed=22, n_surface=2000)
+    xyz = np.round(xyz * 64).astype(np.float32)                 # integer coordinates: translations stay exact
+    r = orc.baseline(xyz)
+    moved = orc.baseline(xyz + np.float32(1024.0))
+    assert np.array_equal(r["keep"], moved["keep"]) and np.array_equal(r["n_i"], moved["n_i"])
+    perm = np.random.default_rng(23).permutation(len(xyz))
+    rp = orc.baseline(xyz[perm])
+    assert np.array_equal(rp["keep"], r["keep"][perm]) and np.array_equal(rp["n_i"], r["n_i"][perm])
