@@ -201,6 +201,31 @@ int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches);
 // the recording instantiation (debug / training outputs), in its own translation unit
 int launch_leaf_rec(const LeafArgs &a, int num_sms, cudaStream_t st);
 
+// Evaluation metrics (Eq. 29-30) and the baseline of Sec. 2.2 (gd_eval.cu).
+struct EvalArgs {
+  const float *clean, *denoised;  // device xyz [n][3]
+  uint32_t na, nb;
+  float *nn_clean, *nn_denoised;  // device [na] / [nb] nearest squared distances, or null
+  double *out;                    // device [3]: mse, chamfer, psnr
+  unsigned char *scratch;         // ev_scratch_bytes(na, nb) bytes, 256-byte aligned
+  Counters *ctr;
+  uint32_t spin_limit;
+};
+struct BaselineArgs {
+  const float *xyz;               // device xyz [n][3]
+  uint32_t n;
+  double G, alpha;                // Eq. 6 and Eq. 7 constants
+  uint8_t *keep;                  // device [n]
+  uint32_t *n_i;                  // device [n] neighbour counts (Eq. 5), or null
+  double *params_out;             // device [5]: centroid x, y, z, R, T; or null
+  unsigned char *scratch;         // ev_scratch_bytes(n, 0) bytes
+  Counters *ctr;
+  uint32_t spin_limit;
+};
+size_t ev_scratch_bytes(uint32_t na, uint32_t nb);
+int launch_eval_metrics(const EvalArgs &e, int num_sms, cudaStream_t st);
+int launch_baseline(const BaselineArgs &b, int num_sms, cudaStream_t st);
+
 struct BackArgs {
   TrainCache train;
   uint32_t n;

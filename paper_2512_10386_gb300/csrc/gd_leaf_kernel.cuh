@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "gd_common.cuh"
+#include "gd_f32x2.cuh"
 #include "gd_knn_select.cuh"
 
 namespace gd {
@@ -44,22 +45,22 @@ struct LeafMem {
   float *r2, *wa;            // [cap] per P_1 position: r_K^2, (alpha/2) ell; wa also holds voxel hash slots
   float *F;                  // [cap] score; shares r2's storage (F_i is written after r2_i's last read)
   uint8_t *flag;             // [cap] 0 removed by density gate, 1 scored, 2 kept
-  void *nbr;                 // neighbour positions: see nb_bits (shared memory) or [KMAX][cap] u32 (global)
+  void *nbr;                 // neighbours: bitmap rows (shared memory, see mask_words) or [KMAX][cap] u32 (global)
   uint32_t hcap, scap, cap;
 };
 
-// Neighbour table of the shared-memory path: query q owns nb_words(cap, kmax)
-// consecutive 32-bit words holding its neighbour positions as nb_bits(cap)-bit
-// fields, rank t at bit t * nb_bits (a 512-point leaf needs 9 bits, not 16).
+// bits of a position in a leaf of `cap` points (the position field of a parked kNN key)
 __host__ __device__ __forceinline__ uint32_t nb_bits(uint32_t cap) {
   uint32_t b = 1;
   while ((1u << b) < cap) ++b;
   return b;
 }
-// an odd word count per query keeps the lanes of a warp on distinct banks
-__host__ __device__ __forceinline__ uint32_t nb_words(uint32_t cap, int kmax) {
-  return (((uint32_t)kmax * nb_bits(cap) + 31u) / 32u) | 1u;
-}
+// Neighbour table of the shared-memory path: a bitmap of positions per query.
+// Query q owns mask_words(cap) consecutive 32-bit words; bit b of word c marks
+// position 32c + b as one of its neighbours.  The kNN records a whole chunk of
+// 32 candidates with one store, and the score visits the neighbours in position
+// order.  An odd word count keeps the lanes of a warp on distinct banks.
+__host__ __device__ __forceinline__ uint32_t mask_words(uint32_t cap) { return ((cap + 31u) / 32u) | 1u; }
 
 // Layout of the per-leaf arrays.  Region A holds the voxel hash table, later
 // (the lifetimes do not overlap) the neighbour table.  Region R holds a
@@ -70,7 +71,7 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
   constexpr bool kSmem = sizeof(IdxT) == 2;
   const uint32_t hcap = pow2ceil(2 * cap), scap = pow2ceil(cap);
   const size_t hash_end = al16((size_t)hcap * 8) + al16((size_t)hcap * 4);
-  const size_t nbr_bytes = kSmem ? al16((size_t)cap * nb_words(cap, kmax) * 4) : al16((size_t)cap * kmax * sizeof(IdxT));
+  const size_t nbr_bytes = kSmem ? al16((size_t)cap * mask_words(cap) * 4) : al16((size_t)cap * kmax * sizeof(IdxT));
   size_t o = al16(hash_end > nbr_bytes ? hash_end : nbr_bytes);
   size_t rbytes = (size_t)scap * 8;
   if (kSmem) {
@@ -292,35 +293,6 @@ __device__ __forceinline__ float sqdist(float xi, float yi, float zi, float xj, 
   return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
-// Packed two-lane FP32 (sm_100 family): each instruction applies the same
-// round-to-nearest operation to both halves of a 64-bit register pair, with
-// subnormals kept, so a lane of the pair equals the scalar __fsub_rn /
-// __fmul_rn / __fmaf_rn bit for bit.
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
-  f32x2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void upk2(f32x2 v, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
-  f32x2 r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-  f32x2 r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-  f32x2 r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-
 // d^2 from the query (packed broadcast QX = (x_i, x_i), ...) to the four
 // candidates j .. j+3 (j a multiple of 4): three 16-byte loads, six packed
 // subtractions and six packed multiply / fused multiply-adds
@@ -449,8 +421,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   const denoise_params &P = A.p;
   const uint32_t lt = lanemask_lt();
   IdxT *nbr = (IdxT *)M.nbr;
-  constexpr bool kPacked = sizeof(IdxT) == 2;  // shared-memory path: bit-packed neighbour table
-  const uint32_t nbB = nb_bits(M.cap), nbW = nb_words(M.cap, KMAX);
+  constexpr bool kPacked = sizeof(IdxT) == 2;  // shared-memory path: neighbour bitmaps
+  const uint32_t nbB = nb_bits(M.cap), mW = mask_words(M.cap);
   float *const X = M.X;
   float *const Y = M.Y;
   float *const Z = M.Z;
@@ -667,21 +639,11 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       // Record neighbour t of this query (position npos, input index g, distance d2).
       // Ranks come in order t = 0, 1, ...: the packed table is filled through a
       // bit buffer, one word store per 32 bits.
-      uint32_t *const nbw = reinterpret_cast<uint32_t *>(M.nbr) + (size_t)qq * nbW;
-      unsigned long long nb_acc = 0;
-      uint32_t nb_n = 0, nb_w = 0;
+      uint32_t *const nbw = reinterpret_cast<uint32_t *>(M.nbr) + (size_t)qq * mW;  // this query's bitmap row
+      // Record neighbour t (position npos, input index g, distance d2) where the
+      // table keeps positions (global path) and in the debug / training outputs.
       auto emit = [&](uint32_t t, uint32_t npos, uint32_t g, float d2) {
-        if constexpr (kPacked) {
-          nb_acc |= (unsigned long long)npos << nb_n;
-          nb_n += nbB;
-          if (nb_n >= 32) {
-            nbw[nb_w++] = (uint32_t)nb_acc;
-            nb_acc >>= 32;
-            nb_n -= 32;
-          }
-        } else {
-          nbr[(size_t)t * cap + qq] = (IdxT)npos;
-        }
+        if constexpr (!kPacked) nbr[(size_t)t * cap + qq] = (IdxT)npos;
         if (kRec && (dbg_n || dbg_d || A.use_train) && rec_index_ok(A, gq)) {
           if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = g;
           if (dbg_d) A.dbg.nbr_d2[(size_t)gq * P.k + t] = d2;
@@ -725,20 +687,26 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         if (n1 - c0 < 32u) keep &= (1u << (n1 - c0)) - 1u;
         uint32_t em = le_lo & keep;
         uint32_t pm = le_hi & ~le_lo & keep;
-        while (em) {
-          const uint32_t ju = c0 + (uint32_t)(__ffs(em) - 1);
-          em &= em - 1u;
-          if (act && a < keff) emit(a, ju, W[ju], (kRec ? sqdist(xq, yq, zq, X[ju], Y[ju], Z[ju]) : 0.0f));
-          ++a;
+        a += __popc(em);
+        np += __popc(pm);
+        if (!act || a > keff) em = 0;                  // nothing to record (a > keff: counts disagree, reported below)
+        if (!act || ties_only || np > kSelBuf) pm = 0;
+        uint32_t t = a - __popc(em), slot = np - __popc(pm);
+        if constexpr (kPacked) {
+          if (act) nbw[c0 >> 5] = em;  // the chunk's neighbours below the boundary bucket, one store
+        }
+        if constexpr (!kPacked || kRec) {
+          while (em) {
+            const uint32_t ju = c0 + (uint32_t)(__ffs(em) - 1);
+            em &= em - 1u;
+            emit(t++, ju, W[ju], (kRec ? sqdist(xq, yq, zq, X[ju], Y[ju], Z[ju]) : 0.0f));
+          }
         }
         while (pm) {
           const uint32_t ju = c0 + (uint32_t)(__ffs(pm) - 1);
           pm &= pm - 1u;
-          if (act && !ties_only && np < kSelBuf) {
-            const int32_t db = __float_as_int(sqdist(xq, yq, zq, X[ju], Y[ju], Z[ju]));
-            pend[np * kLeafThreads + tid] = ((uint32_t)(db - kbase) << pbits) | ju;
-          }
-          ++np;
+          const int32_t db = __float_as_int(sqdist(xq, yq, zq, X[ju], Y[ju], Z[ju]));
+          pend[(slot++) * kLeafThreads + tid] = ((uint32_t)(db - kbase) << pbits) | ju;
         }
       }
       if (act && (a != cut.c_below || np != cut.c_at)) atomicOr(&A.ctr->status, kStInternal);  // passes agree
@@ -746,38 +714,46 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       // d^2 ties straddling the cut are ranked by input index
       float theta = hi_f;
       const bool parked = act && !ties_only;
-      uint32_t K[kSelBuf];
+      {
+        uint32_t K[kSelBuf];
 #pragma unroll
-      for (int i = 0; i < (int)kSelBuf; ++i) K[i] = (parked && (uint32_t)i < np) ? pend[i * kLeafThreads + tid] : 0xFFFFFFFFu;
-      regsort_u<kSelBuf>(K);
-      uint32_t th_off = 0, n_lt = 0, n_eq = 0;
+        for (int i = 0; i < (int)kSelBuf; ++i)
+          K[i] = (parked && (uint32_t)i < np) ? pend[i * kLeafThreads + tid] : 0xFFFFFFFFu;
+        regsort_u<kSelBuf>(K);
+        uint32_t th_off = 0;
 #pragma unroll
-      for (int i = 0; i < (int)kSelBuf; ++i)
-        if ((uint32_t)i + 1u == need) th_off = K[i] >> pbits;
+        for (int i = 0; i < (int)kSelBuf; ++i) {
+          th_off = ((uint32_t)i + 1u == need) ? (K[i] >> pbits) : th_off;
+          if (parked) pend[i * kLeafThreads + tid] = K[i];  // sorted, for the emission loop below
+        }
+        uint32_t n_lt = 0, n_eq = 0;
 #pragma unroll
-      for (int i = 0; i < (int)kSelBuf; ++i) {
-        if ((uint32_t)i < np) {
+        for (int i = 0; i < (int)kSelBuf; ++i) {
           n_lt += (K[i] >> pbits) < th_off;
-          n_eq += (K[i] >> pbits) == th_off;
+          n_eq += (K[i] >> pbits) == th_off;  // padding keys have offsets above any real one
         }
-      }
-      const uint32_t need_eq = need - n_lt;            // of the n_eq keys at the cut distance
-      const bool straddle = parked && n_eq > need_eq;  // rank those by input index
-      if (parked) theta = __int_as_float(kbase + (int32_t)th_off);
-#pragma unroll
-      for (int i = 0; i < (int)kSelBuf; ++i) {
-        const uint32_t off = K[i] >> pbits, ju = K[i] & pmask;
-        bool take = parked && (uint32_t)i < need;
-        if (straddle && (uint32_t)i < np && off == th_off) {
-          const uint32_t gi = W[ju];
-          uint32_t before = 0;
-#pragma unroll
-          for (int j = 0; j < (int)kSelBuf; ++j) {
-            if ((uint32_t)j < np && (K[j] >> pbits) == th_off) before += W[K[j] & pmask] < gi;
+        if (parked) theta = __int_as_float(kbase + (int32_t)th_off);
+        // take the first `need` sorted keys, unless d^2 ties straddle the cut
+        uint32_t take = parked ? ((need >= 32u) ? 0xFFFFFFFFu : ((1u << need) - 1u)) : 0u;
+        const uint32_t need_eq = need - n_lt;
+        if (parked && n_eq > need_eq) {  // rare: rank the keys at the cut distance by input index
+          take = (n_lt >= 32u) ? 0xFFFFFFFFu : ((1u << n_lt) - 1u);
+#pragma unroll 1
+          for (uint32_t i = n_lt; i < n_lt + n_eq; ++i) {
+            const uint32_t gi = W[pend[i * kLeafThreads + tid] & pmask];
+            uint32_t before = 0;
+#pragma unroll 1
+            for (uint32_t j = n_lt; j < n_lt + n_eq; ++j) before += W[pend[j * kLeafThreads + tid] & pmask] < gi;
+            if (before < need_eq) take |= 1u << i;
           }
-          take = before < need_eq;
         }
-        if (take) emit(a++, ju, W[ju], __int_as_float(kbase + (int32_t)off));
+        while (take) {
+          const uint32_t i = (uint32_t)(__ffs(take) - 1);
+          take &= take - 1u;
+          const uint32_t key = pend[i * kLeafThreads + tid], ju = key & pmask;
+          if constexpr (kPacked) nbw[ju >> 5] |= 1u << (ju & 31u);
+          emit(a++, ju, W[ju], __int_as_float(kbase + (int32_t)(key >> pbits)));
+        }
       }
       // exact ties beyond the buffer (lattices, duplicates): one scan per missing
       // neighbour takes the smallest input index above the last one taken
@@ -797,11 +773,27 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           }
         }
         if (r < rounds) {
+          if constexpr (kPacked) nbw[bp >> 5] |= 1u << (bp & 31u);
           emit(a++, bp, bg, hi_f);
           last = bg;
         }
       }
-      if (kPacked && act && nb_n > 0) nbw[nb_w] = (uint32_t)nb_acc;  // last partial word
+      if constexpr (!kPacked) {
+        // the global path's list in position order (the order of the bitmap rows):
+        // the neighbours below the boundary bucket came in order, the rest are inserted
+        if (act) {
+#pragma unroll 1
+          for (uint32_t t = cut.c_below; t < keff && t < a; ++t) {
+            const IdxT v = nbr[(size_t)t * cap + qq];
+            uint32_t u = t;
+            while (u > 0 && nbr[(size_t)(u - 1) * cap + qq] > v) {
+              nbr[(size_t)u * cap + qq] = nbr[(size_t)(u - 1) * cap + qq];
+              --u;
+            }
+            nbr[(size_t)u * cap + qq] = v;
+          }
+        }
+      }
       if (act) {
         if (a != keff) atomicOr(&A.ctr->status, kStInternal);
         const float rt = (theta < delta2) ? delta2 : theta;
@@ -890,20 +882,18 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       // two neighbours per step into two partial sums (independent chains),
       // F = even-rank terms + odd-rank terms
       float F0 = 0.0f, F1 = 0.0f;
-      const uint32_t *nbr_i = reinterpret_cast<const uint32_t *>(M.nbr) + (size_t)i * nbW;
-      unsigned long long r_acc = 0;
-      uint32_t r_n = 0;
-      const uint32_t r_mask = (1u << nbB) - 1u;
+      // neighbours in position order: from the bitmap row (shared memory) or the
+      // position-ordered list (global path)
+      const uint32_t *row = reinterpret_cast<const uint32_t *>(M.nbr) + (size_t)i * mW;
+      uint32_t rc = 0, rm = kPacked ? row[0] : 0u;
+      const uint32_t rwords = (n1 + 31u) >> 5;
       auto next_j = [&](uint32_t t, bool valid) -> uint32_t {  // called for t = 0, 1, ... in order
         if constexpr (kPacked) {
-          if (valid && r_n < nbB) {
-            r_acc |= (unsigned long long)(*nbr_i++) << r_n;
-            r_n += 32;
-          }
-          const uint32_t j = (uint32_t)r_acc & r_mask;
-          r_acc >>= nbB;
-          r_n -= nbB;
-          return j;
+          if (!valid) return 0u;
+          while (rm == 0u && rc + 1 < rwords) rm = row[++rc];
+          const uint32_t j = (rc << 5) + (uint32_t)(__ffs(rm) - 1);  // rm == 0 only if the row is inconsistent
+          rm &= rm - 1u;
+          return j < n1 ? j : 0u;
         } else {
           return valid ? (uint32_t)nbr[(size_t)t * M.cap + i] : 0u;
         }
