@@ -157,6 +157,47 @@ typedef struct denoise_tuning {
 int denoise_set_tuning(denoise_ctx *ctx, const denoise_tuning *t);
 
 /*
+ * Evaluation metrics of Sec. 4.1 between a clean (ground-truth) cloud A and a
+ * denoised cloud B, both float32 xyz [n][3], host or device:
+ *  metrics[0] = MSE of Eq. 29: the mean over A of the squared distance from
+ *               each clean point to its nearest point of B (the paper takes the
+ *               nearest neighbour as the corresponding point);
+ *  metrics[1] = Chamfer distance of Eq. 30: that mean plus the mean over B of the
+ *               squared distance to the nearest point of A;
+ *  metrics[2] = PSNR of Eq. 29, 10 log10(M^2 / MSE), M = the diagonal of A's
+ *               bounding box (the paper's usual choice for M).
+ * `metrics` is a HOST double[3].  nn_clean [n_clean] / nn_denoised
+ * [n_denoised] (host or device, may be NULL) receive the per-point nearest
+ * squared distances.  Every pair of points is compared (exact nearest
+ * neighbours); squared distances are FP32 with the method's operation order,
+ * the means FP64 in a fixed order (deterministic).
+ * Errors: E_INVAL (NULL argument, an empty cloud), E_CAPACITY (a cloud larger
+ * than max_points), E_NONFINITE, E_TIMEOUT, E_CUDA.
+ */
+int denoise_eval_metrics(denoise_ctx *ctx, const float *clean, size_t n_clean, const float *denoised,
+                         size_t n_denoised, double *metrics, float *nn_clean, float *nn_denoised, void *stream);
+
+/*
+ * The gravitational-function baseline of Sec. 2.2 (Eq. 1-9), the paper's
+ * comparison method: centroid theta (Eq. 1), extents H (Eq. 2), radius
+ * R = 6 (HxHy + HxHz + HyHz) / N (Eq. 3), d_i = |p_i - theta| (Eq. 4),
+ * n_i = number of points within R of p_i, itself included (Eq. 5),
+ * F_i = G n_i / d_i^2 (Eq. 6), T = alpha G (Hx + Hy + Hz) / N (Eq. 7); a point is
+ * kept iff F_i >= T / d_i (Eq. 8-9).  The paper sets G = 6.67e-11 and
+ * alpha = 600.  Eq. 3 is not scale-free (an area over a count), so the result
+ * depends on the units of the coordinates, as in the paper.
+ *  xyz [n][3] float32, host or device; mask [n] uint8 (1 = keep), host or
+ *  device; n_i [n] uint32 counts (may be NULL); params HOST double[5] =
+ *  (theta_x, theta_y, theta_z, R, T) (may be NULL).
+ * The neighbour test compares the FP32 squared distance (the method's
+ * operation order) with R^2; every pair is compared.
+ * Errors: E_INVAL (NULL argument, n = 0, G or alpha not positive and finite),
+ * E_CAPACITY (n > max_points), E_NONFINITE, E_TIMEOUT, E_CUDA.
+ */
+int denoise_run_baseline(denoise_ctx *ctx, const float *xyz, size_t n, double G, double alpha, uint8_t *mask,
+                         uint32_t *n_i, double *params, void *stream);
+
+/*
  * Bounded device-side waits.  Two waits in the path can spin: a radix-sort
  * tile waiting for its predecessor's published prefix (decoupled look-back)
  * and the leaf kernel waiting for its bulk copy of a leaf.  Each gives up after

@@ -32,7 +32,7 @@ EXPORTED = [
     "denoise_set_sync", "denoise_set_graphs", "denoise_set_profiling", "denoise_get_status",
     "denoise_get_stats", "denoise_run_debug", "denoise_set_training", "denoise_soft_removal",
     "denoise_backward", "denoise_run_noalloc", "denoise_set_tuning", "denoise_noalloc_scratch_bytes",
-    "denoise_set_wait_limit", "denoise_test_hold_lookback",
+    "denoise_set_wait_limit", "denoise_test_hold_lookback", "denoise_eval_metrics", "denoise_run_baseline",
 ]
 DENOISE_NOALLOC_MAX_POINTS = 16384
 
@@ -116,6 +116,10 @@ def lib():
     L.denoise_set_tuning.argtypes = [_V, ctypes.POINTER(denoise_tuning)]
     L.denoise_set_wait_limit.argtypes = [_V, ctypes.c_uint32]
     L.denoise_test_hold_lookback.argtypes = [_V, ctypes.c_int32]
+    L.denoise_eval_metrics.argtypes = [_V, _V, ctypes.c_size_t, _V, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
+                                       _V, _V, _V]
+    L.denoise_run_baseline.argtypes = [_V, _V, ctypes.c_size_t, ctypes.c_double, ctypes.c_double, _V, _V,
+                                       ctypes.POINTER(ctypes.c_double), _V]
     for name in EXPORTED:
         if name != "denoise_strerror":
             getattr(L, name).restype = ctypes.c_int
@@ -196,6 +200,18 @@ def denoise_set_wait_limit(ctx, iterations: int) -> int:
 
 def denoise_test_hold_lookback(ctx, tile: int) -> int:
     return lib().denoise_test_hold_lookback(ctx, int(tile))
+
+
+def denoise_eval_metrics(ctx, clean_ptr, n_clean, den_ptr, n_den, nn_clean_ptr, nn_den_ptr, stream):
+    m = (ctypes.c_double * 3)()
+    st = lib().denoise_eval_metrics(ctx, clean_ptr, n_clean, den_ptr, n_den, m, nn_clean_ptr, nn_den_ptr, stream)
+    return st, [m[0], m[1], m[2]]
+
+
+def denoise_run_baseline(ctx, xyz_ptr, n, G, alpha, mask_ptr, n_i_ptr, stream):
+    p = (ctypes.c_double * 5)()
+    st = lib().denoise_run_baseline(ctx, xyz_ptr, n, float(G), float(alpha), mask_ptr, n_i_ptr, p, stream)
+    return st, [p[i] for i in range(5)]
 
 
 def denoise_get_status(ctx, stream) -> int:

@@ -178,6 +178,42 @@ class Denoiser:
         out.update(mask=mask, score=score, stage=stage)
         return out
 
+    def eval_metrics(self, clean: torch.Tensor, denoised: torch.Tensor, per_point: bool = False, stream=None):
+        """Evaluation metrics of Sec. 4.1 (``denoise_eval_metrics``): a dict with
+        ``mse`` and ``psnr`` (Eq. 29) and ``chamfer`` (Eq. 30); with ``per_point``
+        also the nearest squared distances of each clean / denoised point."""
+        self._check_xyz(clean)
+        self._check_xyz(denoised)
+        na, nb = clean.shape[0], denoised.shape[0]
+        nn_a = nn_b = None
+        if per_point:
+            nn_a = torch.empty(na, dtype=torch.float32, device=clean.device)
+            nn_b = torch.empty(nb, dtype=torch.float32, device=denoised.device)
+        st, m = N.denoise_eval_metrics(self.ctx, _ptr(clean), na, _ptr(denoised), nb, _ptr(nn_a), _ptr(nn_b),
+                                       _stream_handle(self.device, stream))
+        N.check(st, "denoise_eval_metrics")
+        out = {"mse": m[0], "chamfer": m[1], "psnr": m[2]}
+        if per_point:
+            out.update(nn_clean=nn_a, nn_denoised=nn_b)
+        return out
+
+    def run_baseline(self, xyz: torch.Tensor, G: float = 6.67e-11, alpha: float = 600.0, counts: bool = False,
+                     stream=None) -> dict:
+        """The gravitational-function baseline of Sec. 2.2 (``denoise_run_baseline``):
+        keep mask (Eq. 8-9), optionally the neighbour counts n_i (Eq. 5), and the
+        centroid, R and T (Eq. 1, 3, 7)."""
+        self._check_xyz(xyz)
+        n = xyz.shape[0]
+        mask = torch.empty(n, dtype=torch.uint8, device=xyz.device)
+        n_i = torch.empty(n, dtype=torch.int32, device=xyz.device) if counts else None
+        st, p = N.denoise_run_baseline(self.ctx, _ptr(xyz), n, G, alpha, _ptr(mask), _ptr(n_i),
+                                       _stream_handle(self.device, stream))
+        N.check(st, "denoise_run_baseline")
+        out = {"keep": mask, "theta": p[0:3], "R": p[3], "T": p[4]}
+        if counts:
+            out["n_i"] = n_i
+        return out
+
     def status(self, stream=None) -> int:
         return N.denoise_get_status(self.ctx, _stream_handle(self.device, stream))
 

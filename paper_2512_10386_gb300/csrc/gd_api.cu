@@ -549,6 +549,105 @@ int denoise_set_tuning(denoise_ctx *ctx, const denoise_tuning *t) {
   return DENOISE_OK;
 }
 
+// Host or device input of an evaluation call: device pointers pass through,
+// host arrays are copied into `stage` (context scratch) first.
+static const float *stage_points(const float *p, size_t n, int device, float *stage, cudaStream_t st, int *rc) {
+  const Loc l = locate(p, device);
+  if (l == Loc::kOtherDevice) {
+    *rc = DENOISE_E_INVAL;
+    return nullptr;
+  }
+  if (l == Loc::kDevice) return p;
+  if (cudaMemcpyAsync(stage, p, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st) != cudaSuccess) *rc = cuda_fail();
+  return stage;
+}
+
+int denoise_eval_metrics(denoise_ctx *ctx, const float *clean, size_t n_clean, const float *denoised,
+                         size_t n_denoised, double *metrics, float *nn_clean, float *nn_denoised, void *stream) {
+  if (!ctx || !clean || !denoised || !metrics || n_clean == 0 || n_denoised == 0) return DENOISE_E_INVAL;
+  if (n_clean > ctx->max_points || n_denoised > ctx->max_points) return DENOISE_E_CAPACITY;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DENOISE_E_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t na = (uint32_t)n_clean, nb = (uint32_t)n_denoised;
+  // context scratch: the spill area holds the passes' arrays and any host staging
+  const size_t need = ev_scratch_bytes(na, nb);
+  const size_t stage_a = (need + 255) & ~size_t(255), stage_b = stage_a + ((12ull * na + 255) & ~size_t(255));
+  const size_t total = stage_b + 12ull * nb;
+  if (total > ctx->max_points * (size_t)ctx->big_bpp) return DENOISE_E_CAPACITY;
+  int rc = DENOISE_OK;
+  const float *a = stage_points(clean, na, ctx->device, (float *)(ctx->d_big + stage_a), st, &rc);
+  const float *b = rc ? nullptr : stage_points(denoised, nb, ctx->device, (float *)(ctx->d_big + stage_b), st, &rc);
+  if (rc) return rc;
+  const Loc la = nn_clean ? locate(nn_clean, ctx->device) : Loc::kDevice;
+  const Loc lb = nn_denoised ? locate(nn_denoised, ctx->device) : Loc::kDevice;
+  if (la == Loc::kOtherDevice || lb == Loc::kOtherDevice) return DENOISE_E_INVAL;
+  EvalArgs e{};
+  e.clean = a;
+  e.denoised = b;
+  e.na = na;
+  e.nb = nb;
+  e.nn_clean = nn_clean ? (la == Loc::kDevice ? nn_clean : ctx->d_score) : nullptr;
+  e.nn_denoised = nn_denoised ? (lb == Loc::kDevice ? nn_denoised : (float *)ctx->d_gin) : nullptr;
+  e.out = ctx->d_grad;
+  e.scratch = ctx->d_big;
+  e.ctr = ctx->d_ctr;
+  e.spin_limit = ctx->wait_limit;
+  if (cudaMemsetAsync(&ctx->d_ctr->status, 0, sizeof(uint32_t), st) != cudaSuccess) return cuda_fail();
+  if (launch_eval_metrics(e, ctx->num_sms, st)) return cuda_fail();
+  if (nn_clean && la == Loc::kHost) cudaMemcpyAsync(nn_clean, e.nn_clean, 4ull * na, cudaMemcpyDeviceToHost, st);
+  if (nn_denoised && lb == Loc::kHost)
+    cudaMemcpyAsync(nn_denoised, e.nn_denoised, 4ull * nb, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(ctx->h_grad, ctx->d_grad, sizeof(double) * 3, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&ctx->h_ctr->status, &ctx->d_ctr->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_fail();
+  const int s2 = map_status(ctx->h_ctr->status);
+  if (s2) return s2;
+  for (int i = 0; i < 3; ++i) metrics[i] = ctx->h_grad[i];
+  return DENOISE_OK;
+}
+
+int denoise_run_baseline(denoise_ctx *ctx, const float *xyz, size_t n, double G, double alpha, uint8_t *mask,
+                         uint32_t *n_i, double *params, void *stream) {
+  if (!ctx || !xyz || !mask || n == 0 || !(G > 0.0) || !isfinite(G) || !(alpha > 0.0) || !isfinite(alpha))
+    return DENOISE_E_INVAL;
+  if (n > ctx->max_points) return DENOISE_E_CAPACITY;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DENOISE_E_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t nn = (uint32_t)n;
+  const size_t need = ev_scratch_bytes(nn, 0);
+  const size_t stage = (need + 255) & ~size_t(255);
+  if (stage + 12ull * nn > ctx->max_points * (size_t)ctx->big_bpp) return DENOISE_E_CAPACITY;
+  int rc = DENOISE_OK;
+  const float *x = stage_points(xyz, nn, ctx->device, (float *)(ctx->d_big + stage), st, &rc);
+  if (rc) return rc;
+  const Loc lm = locate(mask, ctx->device), ln = n_i ? locate(n_i, ctx->device) : Loc::kDevice;
+  if (lm == Loc::kOtherDevice || ln == Loc::kOtherDevice) return DENOISE_E_INVAL;
+  BaselineArgs b{};
+  b.xyz = x;
+  b.n = nn;
+  b.G = G;
+  b.alpha = alpha;
+  b.keep = lm == Loc::kDevice ? mask : ctx->d_mask;
+  b.n_i = n_i ? (ln == Loc::kDevice ? n_i : (uint32_t *)ctx->d_gin) : nullptr;
+  b.params_out = ctx->d_partials;
+  b.scratch = ctx->d_big;
+  b.ctr = ctx->d_ctr;
+  b.spin_limit = ctx->wait_limit;
+  if (cudaMemsetAsync(&ctx->d_ctr->status, 0, sizeof(uint32_t), st) != cudaSuccess) return cuda_fail();
+  if (launch_baseline(b, ctx->num_sms, st)) return cuda_fail();
+  if (lm == Loc::kHost) cudaMemcpyAsync(mask, b.keep, nn, cudaMemcpyDeviceToHost, st);
+  if (n_i && ln == Loc::kHost) cudaMemcpyAsync(n_i, b.n_i, 4ull * nn, cudaMemcpyDeviceToHost, st);
+  double hp[5] = {0, 0, 0, 0, 0};
+  if (params) cudaMemcpyAsync(hp, ctx->d_partials, sizeof(hp), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&ctx->h_ctr->status, &ctx->d_ctr->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_fail();
+  const int s2 = map_status(ctx->h_ctr->status);
+  if (s2) return s2;
+  if (params)
+    for (int i = 0; i < 5; ++i) params[i] = hp[i];
+  return DENOISE_OK;
+}
+
 int denoise_set_wait_limit(denoise_ctx *ctx, uint32_t iterations) {
   if (!ctx) return DENOISE_E_INVAL;
   ctx->wait_limit = iterations;

@@ -157,7 +157,7 @@ namespace {
 // ratio is largest for small caps (fixed-size parts); beyond 2^16 points it only
 // falls, so scanning 65..65536 bounds every size.
 uint32_t big_bpp_scan(int kmax) {
-  size_t worst = 0;
+  size_t worst = 4u * ((kLeafSmemMax + 31u) / 32u);
   for (uint32_t cap = 65; cap <= 65536; ++cap) {
     const size_t b = carve<uint32_t>(nullptr, cap, kmax, nullptr);
     const size_t per = (b + cap - 1) / cap;
@@ -168,13 +168,16 @@ uint32_t big_bpp_scan(int kmax) {
 }  // namespace
 
 uint32_t leaf_big_bpp(int kmax) {
-  // computed once, on first use, for the four list sizes (thread-safe static init)
+  // computed once, on first use, for the four list sizes (thread-safe static init);
+  // at least the neighbour bitmap of a shared-memory leaf (one word a point per
+  // 32 points of the leaf), which may be kept in the spill area
   static const uint32_t table[4] = {big_bpp_scan(8), big_bpp_scan(16), big_bpp_scan(32), big_bpp_scan(64)};
   return table[kmax <= 8 ? 0 : kmax <= 16 ? 1 : kmax <= 32 ? 2 : 3];
 }
 
 uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit) {
   uint32_t l = pow2ceil(leaf_capacity < 64 ? 64 : leaf_capacity);
+  if (l > kLeafSmemMax) l = kLeafSmemMax;
   while (l > 64 && leaf_smem_bytes(l, kmax) > smem_limit) l >>= 1;
   return l;
 }

@@ -45,7 +45,8 @@ struct LeafMem {
   float *r2, *wa;            // [cap] per P_1 position: r_K^2, (alpha/2) ell; wa also holds voxel hash slots
   float *F;                  // [cap] score; shares r2's storage (F_i is written after r2_i's last read)
   uint8_t *flag;             // [cap] 0 removed by density gate, 1 scored, 2 kept
-  void *nbr;                 // neighbours: bitmap rows (shared memory, see mask_words) or [KMAX][cap] u32 (global)
+  void *nbr;                 // neighbours: bitmaps (shared-memory path, see bitmap_words) or [KMAX][cap] u32 (global)
+  uint32_t nbr_bytes;        // bytes of the region that holds nbr
   uint32_t hcap, scap, cap;
 };
 
@@ -55,12 +56,14 @@ __host__ __device__ __forceinline__ uint32_t nb_bits(uint32_t cap) {
   while ((1u << b) < cap) ++b;
   return b;
 }
-// Neighbour table of the shared-memory path: a bitmap of positions per query.
-// Query q owns mask_words(cap) consecutive 32-bit words; bit b of word c marks
-// position 32c + b as one of its neighbours.  The kNN records a whole chunk of
-// 32 candidates with one store, and the score visits the neighbours in position
-// order.  An odd word count keeps the lanes of a warp on distinct banks.
-__host__ __device__ __forceinline__ uint32_t mask_words(uint32_t cap) { return ((cap + 31u) / 32u) | 1u; }
+// Neighbour table of the shared-memory path: a bitmap of neighbour positions,
+// word (c, q) at index c * n1 + q holding bit b for position 32c + b among query
+// q's neighbours (chunk-major: a warp's 32 queries touch 32 consecutive words).
+// The kNN records a whole chunk of 32 candidates with one store, the score walks
+// the neighbours in position order.  The table lives in region A (after the
+// voxel hash is done with it) when it fits there, else in the leaf's part of
+// the global spill area (L2-resident), through the same generic pointer.
+__host__ __device__ __forceinline__ uint32_t bitmap_words(uint32_t n1) { return ((n1 + 31u) / 32u) * n1; }
 
 // Layout of the per-leaf arrays.  Region A holds the voxel hash table, later
 // (the lifetimes do not overlap) the neighbour table.  Region R holds a
@@ -71,7 +74,7 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
   constexpr bool kSmem = sizeof(IdxT) == 2;
   const uint32_t hcap = pow2ceil(2 * cap), scap = pow2ceil(cap);
   const size_t hash_end = al16((size_t)hcap * 8) + al16((size_t)hcap * 4);
-  const size_t nbr_bytes = kSmem ? al16((size_t)cap * mask_words(cap) * 4) : al16((size_t)cap * kmax * sizeof(IdxT));
+  const size_t nbr_bytes = kSmem ? hash_end : al16((size_t)cap * kmax * sizeof(IdxT));
   size_t o = al16(hash_end > nbr_bytes ? hash_end : nbr_bytes);
   size_t rbytes = (size_t)scap * 8;
   if (kSmem) {
@@ -83,6 +86,7 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
     m->hkey = (unsigned long long *)base;
     m->hcnt = (uint32_t *)(base + al16((size_t)hcap * 8));
     m->nbr = (void *)base;
+    m->nbr_bytes = (uint32_t)o;
     m->hcap = hcap;
     m->scap = scap;
     m->cap = cap;
@@ -422,7 +426,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   const uint32_t lt = lanemask_lt();
   IdxT *nbr = (IdxT *)M.nbr;
   constexpr bool kPacked = sizeof(IdxT) == 2;  // shared-memory path: neighbour bitmaps
-  const uint32_t nbB = nb_bits(M.cap), mW = mask_words(M.cap);
+  const uint32_t nbB = nb_bits(M.cap);
   float *const X = M.X;
   float *const Y = M.Y;
   float *const Z = M.Z;
@@ -523,6 +527,10 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     return;
   }
   const uint32_t keff = (P.k < n1 - 1) ? P.k : n1 - 1;
+  // the neighbour bitmap (shared-memory path): region A if it fits, else the spill area
+  uint32_t *const tbl = (bitmap_words(n1) * 4u <= M.nbr_bytes)
+                            ? reinterpret_cast<uint32_t *>(M.nbr)
+                            : reinterpret_cast<uint32_t *>(A.big_scratch + (size_t)lf.start * A.big_bpp);
   if (tid == 0) {
     atomicAdd(&A.ctr->knn_pairs, (unsigned long long)n1 * (unsigned long long)(n1 - 1));
     atomicAdd(&A.ctr->n_p1, (unsigned long long)n1);
@@ -639,7 +647,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       // Record neighbour t of this query (position npos, input index g, distance d2).
       // Ranks come in order t = 0, 1, ...: the packed table is filled through a
       // bit buffer, one word store per 32 bits.
-      uint32_t *const nbw = reinterpret_cast<uint32_t *>(M.nbr) + (size_t)qq * mW;  // this query's bitmap row
+      uint32_t *const nbw = tbl + qq;  // this query's bitmap column: word c at nbw[c * n1]
       // Record neighbour t (position npos, input index g, distance d2) where the
       // table keeps positions (global path) and in the debug / training outputs.
       auto emit = [&](uint32_t t, uint32_t npos, uint32_t g, float d2) {
@@ -693,7 +701,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         if (!act || ties_only || np > kSelBuf) pm = 0;
         uint32_t t = a - __popc(em), slot = np - __popc(pm);
         if constexpr (kPacked) {
-          if (act) nbw[c0 >> 5] = em;  // the chunk's neighbours below the boundary bucket, one store
+          if (act) nbw[(size_t)(c0 >> 5) * n1] = em;  // the chunk's neighbours below the boundary bucket, one store
         }
         if constexpr (!kPacked || kRec) {
           while (em) {
@@ -751,7 +759,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           const uint32_t i = (uint32_t)(__ffs(take) - 1);
           take &= take - 1u;
           const uint32_t key = pend[i * kLeafThreads + tid], ju = key & pmask;
-          if constexpr (kPacked) nbw[ju >> 5] |= 1u << (ju & 31u);
+          if constexpr (kPacked) nbw[(size_t)(ju >> 5) * n1] |= 1u << (ju & 31u);
           emit(a++, ju, W[ju], __int_as_float(kbase + (int32_t)(key >> pbits)));
         }
       }
@@ -773,7 +781,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           }
         }
         if (r < rounds) {
-          if constexpr (kPacked) nbw[bp >> 5] |= 1u << (bp & 31u);
+          if constexpr (kPacked) nbw[(size_t)(bp >> 5) * n1] |= 1u << (bp & 31u);
           emit(a++, bp, bg, hi_f);
           last = bg;
         }
@@ -884,13 +892,13 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       float F0 = 0.0f, F1 = 0.0f;
       // neighbours in position order: from the bitmap row (shared memory) or the
       // position-ordered list (global path)
-      const uint32_t *row = reinterpret_cast<const uint32_t *>(M.nbr) + (size_t)i * mW;
+      const uint32_t *row = tbl + i;  // word c at row[c * n1]
       uint32_t rc = 0, rm = kPacked ? row[0] : 0u;
       const uint32_t rwords = (n1 + 31u) >> 5;
       auto next_j = [&](uint32_t t, bool valid) -> uint32_t {  // called for t = 0, 1, ... in order
         if constexpr (kPacked) {
           if (!valid) return 0u;
-          while (rm == 0u && rc + 1 < rwords) rm = row[++rc];
+          while (rm == 0u && rc + 1 < rwords) rm = row[(size_t)(++rc) * n1];
           const uint32_t j = (rc << 5) + (uint32_t)(__ffs(rm) - 1);  // rm == 0 only if the row is inconsistent
           rm &= rm - 1u;
           return j < n1 ? j : 0u;
@@ -998,13 +1006,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, uint32_t
   return false;
 }
 
-// 5 CTAs of 128 threads per SM for K <= 32 (a 512-point, K = 32 leaf takes 39 KB
-// of shared memory, and at most 102 registers a thread fit 5 CTAs); the K = 64
-// tables need more shared memory.  kRec: the debug / training outputs are
-// written (a separate instantiation, so that the plain path carries none of
-// their code).
+// Persistent CTAs of 128 threads, GD_LEAF_MIN_CTAS per SM for K <= 32 (a
+// 512-point leaf takes 33 KB of shared memory, so 6 fit; the register bound
+// follows from the count).  kRec: the debug / training outputs are written (a
+// separate instantiation, so that the plain path carries none of their code).
+#ifndef GD_LEAF_MIN_CTAS
+#define GD_LEAF_MIN_CTAS 6
+#endif
 template <int KMAX, bool kRec>
-__global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : 5) k_leaf(const LeafArgs A) {
+__global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : GD_LEAF_MIN_CTAS) k_leaf(const LeafArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long s_mbar;
   __shared__ LeafShared S;
