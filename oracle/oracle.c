@@ -47,6 +47,7 @@
  *  R11 Top-lambda (end of Sec. 3): keep ceil(lambda*|P_2|) points of each
  *     leaf by (F descending, input index ascending).  Mode 1 instead keeps
  *     ln F >= tau (the differentiable form).
+ *  R13 structural variants (ablations of Sec. 4.3.2): see process_leaf.
  *  R12 differentiable form: removal probability r_i = 1 - sigmoid((ln F_i -
  *     tau)/T) on P_2 and 1 elsewhere; soft-F1 = 2 sum(r y)/(sum r + sum y)
  *     (Eq. 26-28 with soft counts); loss = 1 - soft-F1.
@@ -189,9 +190,64 @@ static float sq_dist(const ctx_t *c, uint32_t i, uint32_t j) {
   return fmaf(dz, dz, fmaf(dy, dy, xx));
 }
 
+/* R6, R7 and Eq. 13 for every point of a list: its k_eff nearest among the
+ * others of the list (positions into the list), the floored k_eff-th squared
+ * distance and the density.  With `record`, the debug outputs are written. */
+static int knn_list(ctx_t *c, const uint32_t *pts, uint32_t n1, uint32_t keff, uint32_t *nb, float *nd2,
+                    float *r2, double *rho, int record) {
+  const orc_params *p = c->p;
+  orc_out *o = c->out;
+  cand_t *cand = (cand_t *)malloc(sizeof(cand_t) * n1);
+  if (!cand) return ORC_ENOMEM;
+  const uint32_t *p1 = pts;
+  const float delta2 = c->delta * c->delta;
+  for (uint32_t a = 0; a < n1; ++a) {
+    uint32_t m = 0;
+    for (uint32_t b = 0; b < n1; ++b) {
+      if (b == a) continue;
+      cand[m].d2 = sq_dist(c, p1[a], p1[b]);
+      cand[m].idx = p1[b];
+      cand[m].pos = b;
+      ++m;
+    }
+    qsort(cand, m, sizeof(cand_t), cmp_cand);
+    for (uint32_t s = 0; s < keff; ++s) {
+      nb[(size_t)a * keff + s] = cand[s].pos;
+      nd2[(size_t)a * keff + s] = cand[s].d2;
+    }
+    float rk2 = cand[keff - 1].d2;
+    r2[a] = (rk2 < delta2) ? delta2 : rk2;
+    /* Eq. 13 */
+    double rr = (double)r2[a];
+    rho[a] = (double)keff / ((4.0 / 3.0) * PI_D * (rr * sqrt(rr)));
+    if (!record) continue;
+    if (o->r2) o->r2[p1[a]] = r2[a];
+    if (o->rho) o->rho[p1[a]] = rho[a];
+    if (o->nbr)
+      for (uint32_t s = 0; s < p->k; ++s)
+        o->nbr[(size_t)p1[a] * p->k + s] = (s < keff) ? cand[s].idx : NONE32;
+    if (o->nbr_d2)
+      for (uint32_t s = 0; s < p->k; ++s)
+        o->nbr_d2[(size_t)p1[a] * p->k + s] = (s < keff) ? cand[s].d2 : 0.0f;
+  }
+  free(cand);
+  return ORC_OK;
+}
+
+/* Structural variants (Sec. 4.3.2, Tables 8-9), reading R13:
+ *  stage_off bit 0: no voxel gate (A1): P_1 = the leaf's points;
+ *  stage_off bit 1: no density gate (A2): P_2 = P_1, and a point with no
+ *                   possible neighbour is scored (F = 0) instead of removed;
+ *  stage_off bit 2: no score selection (A3): every point of P_2 is kept, with
+ *                   score 0; without A2 as well, no kNN is computed at all;
+ *  rescore_p2:      the score uses a second kNN computed within P_2 (its own
+ *                   k_eff, r_K and densities, and rho_med over them) instead of
+ *                   the kNN on P_1 (the other reading of Eq. 21).
+ * "Without octree" (Table 8) is leaf_capacity >= N: the root is the only leaf. */
 static int process_leaf(ctx_t *c, const keyed_t *sorted, const leaf_t *lf, uint32_t leaf_id) {
   const orc_params *p = c->p;
   orc_out *o = c->out;
+  const int a1_on = !(p->stage_off & 1u), a2_on = !(p->stage_off & 2u), a3_on = !(p->stage_off & 4u);
   const uint32_t nt = lf->count;
   uint32_t *idx = (uint32_t *)malloc(sizeof(uint32_t) * nt);
   uint32_t *vox = (uint32_t *)malloc(sizeof(uint32_t) * nt * 3);
@@ -229,13 +285,18 @@ static int process_leaf(ctx_t *c, const keyed_t *sorted, const leaf_t *lf, uint3
     }
   uint32_t n1 = 0;
   for (uint32_t t = 0; t < nt; ++t) {
+    if (o->leaf_of) o->leaf_of[idx[t]] = leaf_id;
+    if (!a1_on) {  /* the voxel gate is off: every point is in P_1 */
+      if (o->vox_count) o->vox_count[idx[t]] = 0;
+      p1[n1++] = idx[t];
+      continue;
+    }
     uint32_t k = 0;
     for (uint32_t s = 0; s < nt; ++s)
       k += (vox[3 * s] == vox[3 * t] && vox[3 * s + 1] == vox[3 * t + 1] &&
             vox[3 * s + 2] == vox[3 * t + 2]);
     cnt[t] = k;
     if (o->vox_count) o->vox_count[idx[t]] = k;
-    if (o->leaf_of) o->leaf_of[idx[t]] = leaf_id;
     if (k >= p->min_vox_count) p1[n1++] = idx[t];
     else c->stage_all[idx[t]] = 1;
   }
@@ -245,88 +306,102 @@ static int process_leaf(ctx_t *c, const keyed_t *sorted, const leaf_t *lf, uint3
   if (o->leaf_n2) o->leaf_n2[leaf_id] = 0;
   if (o->leaf_rho_med) o->leaf_rho_med[leaf_id] = 0.0;
 
-  if (n1 <= 1) {  /* R6: not enough support for a neighbour */
+  if (!a2_on && !a3_on) {  /* neither gate nor score needs a neighbour: P_1 is kept */
+    if (o->leaf_n2) o->leaf_n2[leaf_id] = n1;
+    free(idx); free(vox); free(cnt); free(p1);
+    return ORC_OK;
+  }
+  if (n1 <= 1 && a2_on) {  /* R6: not enough support for a neighbour */
     for (uint32_t t = 0; t < n1; ++t) c->stage_all[p1[t]] = 2;
     free(idx); free(vox); free(cnt); free(p1);
     return ORC_OK;
   }
 
   /* kNN on P_1 (R6, R7) */
-  const uint32_t keff = (p->k < n1 - 1) ? p->k : n1 - 1;
-  uint32_t *nb = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n1 * keff);   /* P_1 positions */
-  float *nd2 = (float *)malloc(sizeof(float) * (size_t)n1 * keff);
+  const uint32_t keff = (n1 <= 1) ? 0 : (p->k < n1 - 1) ? p->k : n1 - 1;
+  const size_t nk = (size_t)n1 * (keff ? keff : 1);
+  uint32_t *nb = (uint32_t *)malloc(sizeof(uint32_t) * nk);   /* P_1 positions */
+  float *nd2 = (float *)malloc(sizeof(float) * nk);
   float *r2 = (float *)malloc(sizeof(float) * n1);
   double *rho = (double *)malloc(sizeof(double) * n1);
-  cand_t *cand = (cand_t *)malloc(sizeof(cand_t) * n1);
-  if (!nb || !nd2 || !r2 || !rho || !cand) return ORC_ENOMEM;
-  const float delta2 = c->delta * c->delta;
-  for (uint32_t a = 0; a < n1; ++a) {
-    uint32_t m = 0;
-    for (uint32_t b = 0; b < n1; ++b) {
-      if (b == a) continue;
-      cand[m].d2 = sq_dist(c, p1[a], p1[b]);
-      cand[m].idx = p1[b];
-      cand[m].pos = b;
-      ++m;
-    }
-    qsort(cand, m, sizeof(cand_t), cmp_cand);
-    for (uint32_t s = 0; s < keff; ++s) {
-      nb[(size_t)a * keff + s] = cand[s].pos;
-      nd2[(size_t)a * keff + s] = cand[s].d2;
-    }
-    float rk2 = cand[keff - 1].d2;
-    r2[a] = (rk2 < delta2) ? delta2 : rk2;
-    /* Eq. 13 */
-    double rr = (double)r2[a];
-    rho[a] = (double)keff / ((4.0 / 3.0) * PI_D * (rr * sqrt(rr)));
-    if (o->r2) o->r2[p1[a]] = r2[a];
-    if (o->rho) o->rho[p1[a]] = rho[a];
-    if (o->nbr)
-      for (uint32_t s = 0; s < p->k; ++s)
-        o->nbr[(size_t)p1[a] * p->k + s] = (s < keff) ? cand[s].idx : NONE32;
-    if (o->nbr_d2)
-      for (uint32_t s = 0; s < p->k; ++s)
-        o->nbr_d2[(size_t)p1[a] * p->k + s] = (s < keff) ? cand[s].d2 : 0.0f;
-  }
-
-  /* Eq. 14 with R8: exact hazen percentile of rho over the leaf's P_1 */
   double *sorted_rho = (double *)malloc(sizeof(double) * n1);
   uint8_t *in2 = (uint8_t *)malloc(n1);
-  if (!sorted_rho || !in2) return ORC_ENOMEM;
-  memcpy(sorted_rho, rho, sizeof(double) * n1);
-  qsort(sorted_rho, n1, sizeof(double), cmp_double);
-  double pos = (double)n1 * (double)p->rho_percentile / 100.0 + 0.5;
-  double cc = ceil(pos);
-  uint32_t crank = (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;
-  double thr = sorted_rho[crank - 1];
+  if (!nb || !nd2 || !r2 || !rho || !sorted_rho || !in2) return ORC_ENOMEM;
+  if (keff && knn_list(c, p1, n1, keff, nb, nd2, r2, rho, 1)) return ORC_ENOMEM;
+
+  /* Eq. 14 with R8: exact hazen percentile of rho over the leaf's P_1 */
   uint32_t m2 = 0;
-  for (uint32_t a = 0; a < n1; ++a) {
-    in2[a] = rho[a] >= thr;
-    if (in2[a]) sorted_rho[m2++] = rho[a];
-    else c->stage_all[p1[a]] = 2;
+  if (a2_on) {
+    memcpy(sorted_rho, rho, sizeof(double) * n1);
+    qsort(sorted_rho, n1, sizeof(double), cmp_double);
+    double pos = (double)n1 * (double)p->rho_percentile / 100.0 + 0.5;
+    double cc = ceil(pos);
+    uint32_t crank = (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;
+    double thr = sorted_rho[crank - 1];
+    for (uint32_t a = 0; a < n1; ++a) {
+      in2[a] = rho[a] >= thr;
+      if (in2[a]) sorted_rho[m2++] = rho[a];
+      else c->stage_all[p1[a]] = 2;
+    }
+  } else {
+    for (uint32_t a = 0; a < n1; ++a) {
+      in2[a] = 1;
+      if (keff) sorted_rho[m2] = rho[a];
+      ++m2;
+    }
+  }
+  if (o->leaf_n2) o->leaf_n2[leaf_id] = m2;
+  if (!a3_on) {  /* no score selection: P_2 is kept */
+    free(sorted_rho); free(in2);
+    free(nb); free(nd2); free(r2); free(rho);
+    free(idx); free(vox); free(cnt); free(p1);
+    return ORC_OK;
+  }
+
+  /* The set the score runs on: P_1 with the P_2 flags (reading R10), or P_2
+   * alone with its own kNN (rescore_p2). */
+  uint32_t ns = n1, ks = keff;
+  uint32_t *set = p1;
+  uint32_t *p2 = NULL;
+  if (p->rescore_p2) {
+    p2 = (uint32_t *)malloc(sizeof(uint32_t) * (m2 ? m2 : 1));
+    if (!p2) return ORC_ENOMEM;
+    uint32_t t2 = 0;
+    for (uint32_t a = 0; a < n1; ++a)
+      if (in2[a]) p2[t2++] = p1[a];
+    ns = m2;
+    ks = (ns <= 1) ? 0 : (p->k < ns - 1) ? p->k : ns - 1;
+    if (ks && knn_list(c, p2, ns, ks, nb, nd2, r2, rho, 1)) return ORC_ENOMEM;
+    for (uint32_t a = 0; a < ns; ++a) {
+      in2[a] = 1;
+      sorted_rho[a] = rho[a];
+    }
+    set = p2;
   }
 
   /* Eq. 16 with R9: median of rho over P_2 */
-  qsort(sorted_rho, m2, sizeof(double), cmp_double);
-  double rho_med = (m2 & 1u) ? sorted_rho[(m2 - 1) / 2]
-                             : 0.5 * (sorted_rho[m2 / 2 - 1] + sorted_rho[m2 / 2]);
+  double rho_med = 0.0;
+  if (ks) {
+    qsort(sorted_rho, m2, sizeof(double), cmp_double);
+    rho_med = (m2 & 1u) ? sorted_rho[(m2 - 1) / 2]
+                        : 0.5 * (sorted_rho[m2 / 2 - 1] + sorted_rho[m2 / 2]);
+  }
   if (o->leaf_rho_med) o->leaf_rho_med[leaf_id] = rho_med;
-  if (o->leaf_n2) o->leaf_n2[leaf_id] = m2;
 
-  /* Eq. 15-21 with R10: dual-weight gravitational score */
+  /* Eq. 15-21 with R10: dual-weight gravitational score (an empty neighbour set scores 0) */
   const double alpha = p->alpha, sigma = p->sigma, gamma = p->gamma;
   const double eps_rho = p->eps_rho, eps_k = p->eps_k;
   const double wden_den = rho_med * rho_med + eps_rho;
   ranked_t *rk = (ranked_t *)malloc(sizeof(ranked_t) * (m2 ? m2 : 1));
   if (!rk) return ORC_ENOMEM;
   uint32_t r = 0;
-  for (uint32_t a = 0; a < n1; ++a) {
+  for (uint32_t a = 0; a < ns; ++a) {
     if (!in2[a]) continue;
     double F = 0.0, dA = 0.0, dS = 0.0, dG = 0.0;
-    const double r2i = (double)r2[a];
-    for (uint32_t s = 0; s < keff; ++s) {
-      uint32_t b = nb[(size_t)a * keff + s];
-      double d2 = (double)nd2[(size_t)a * keff + s];
+    const double r2i = ks ? (double)r2[a] : 0.0;
+    for (uint32_t s = 0; s < ks; ++s) {
+      uint32_t b = nb[(size_t)a * ks + s];
+      double d2 = (double)nd2[(size_t)a * ks + s];
       double W = rho[a] * rho[b] / wden_den;                      /* Eq. 17 base */
       double w_den = pow(W, alpha / 2.0);                         /* Eq. 17      */
       double w_dis = exp(-d2 / (2.0 * (sigma * sigma) * r2i));    /* Eq. 18-19   */
@@ -340,14 +415,14 @@ static int process_leaf(ctx_t *c, const keyed_t *sorted, const leaf_t *lf, uint3
         if (d2 > 0.0) dG += -t * D * 0.5 * log(d2) / (D + eps_k);
       }
     }
-    c->F_all[p1[a]] = F;
+    c->F_all[set[a]] = F;
     if (c->dF) {
-      c->dF[3 * (size_t)p1[a] + 0] = dA;
-      c->dF[3 * (size_t)p1[a] + 1] = dS;
-      c->dF[3 * (size_t)p1[a] + 2] = dG;
+      c->dF[3 * (size_t)set[a] + 0] = dA;
+      c->dF[3 * (size_t)set[a] + 1] = dS;
+      c->dF[3 * (size_t)set[a] + 2] = dG;
     }
     rk[r].f = F;
-    rk[r].idx = p1[a];
+    rk[r].idx = set[a];
     rk[r].pos = a;
     ++r;
   }
@@ -363,8 +438,8 @@ static int process_leaf(ctx_t *c, const keyed_t *sorted, const leaf_t *lf, uint3
       c->stage_all[rk[t].idx] = (log(rk[t].f) >= (double)p->tau) ? 0 : 3;
   }
 
-  free(rk); free(sorted_rho); free(in2);
-  free(nb); free(nd2); free(r2); free(rho); free(cand);
+  free(rk); free(sorted_rho); free(in2); free(p2);
+  free(nb); free(nd2); free(r2); free(rho);
   free(idx); free(vox); free(cnt); free(p1);
   return ORC_OK;
 }
@@ -382,6 +457,7 @@ static int check_params(const orc_params *p) {
   if (!isfinite(p->alpha) || !(p->eps_rho >= 0.0f) || !(p->eps_k >= 0.0f)) return ORC_EINVAL;
   if (p->select_mode > 1) return ORC_EINVAL;
   if (!(p->temperature > 0.0f)) return ORC_EINVAL;
+  if (p->stage_off > 7u || p->rescore_p2 > 1u) return ORC_EINVAL;
   return ORC_OK;
 }
 

@@ -34,6 +34,9 @@ typedef struct {
   float lambda;            /* Top-lambda keep ratio                                 */
   float tau;               /* log-score threshold (mode 1)                          */
   float temperature;       /* soft-mask temperature (differentiable form)           */
+  uint32_t stage_off;      /* ablations (Table 9): bit 0 no voxel gate (A1), bit 1 no density
+                              gate (A2), bit 2 no score selection (A3); 0 = the method         */
+  uint32_t rescore_p2;     /* 1: the score uses a kNN recomputed within P_2               */
 } orc_params;
 
 /* Outputs; every pointer may be NULL.  Per-point arrays are in input order. */

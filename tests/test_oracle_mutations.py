@@ -55,6 +55,9 @@ MUTATIONS = [
     ("baseline Eq. 8 with d^2", "keep[i] = F >= T / d;", "keep[i] = F >= T / (d * d);"),
     ("baseline centroid over N-1", "for (int c = 0; c < 3; ++c) theta[c] /= (double)n;",
      "for (int c = 0; c < 3; ++c) theta[c] /= (double)(n - 1);"),
+    ("variant: voxel gate never switched off", "    if (!a1_on) {  /* the voxel gate is off", "    if (0) {  /* the voxel gate is off"),
+    ("variant: score selection never switched off", "  if (!a3_on) {  /* no score selection", "  if (0) {  /* no score selection"),
+    ("variant: rescoring ignored", "  if (p->rescore_p2) {", "  if (0) {"),
     ("voxel origin shifted", "float d = coord(c, idx[t], a) - lo[a];", "float d = coord(c, idx[t], a) - lo[a] + h * 0.5f;"),
 ]
 

@@ -690,3 +690,71 @@ def test_baseline_translation_and_permutation_invariance(orc):
     perm = np.random.default_rng(23).permutation(len(xyz))
     rp = orc.baseline(xyz[perm])
     assert np.array_equal(rp["keep"], r["keep"][perm]) and np.array_equal(rp["n_i"], r["n_i"][perm])
+
+
+# --------------------------------------------------------------------------
+# structural variants (Sec. 4.3.2, Tables 8-9; reading R13), each against an
+# equivalent configuration of the full method
+# --------------------------------------------------------------------------
+def _variant_cloud():
+    from synth import object_cloud
+    xyz, _ = object_cloud(seed=24, n_surface=4000)
+    return xyz
+
+
+def test_without_voxel_gate_equals_occupancy_one(orc):
+    xyz = _variant_cloud()
+    off = orc.denoise(xyz, _params(orc, k=12, beta=3.0, stage_off=1))
+    nv1 = orc.denoise(xyz, _params(orc, k=12, beta=3.0, min_vox_count=1))   # every voxel holds >= 1 point
+    assert not (off["stage"] == 1).any()
+    assert np.array_equal(off["stage"], nv1["stage"]) and np.array_equal(off["score"], nv1["score"])
+
+
+def test_without_density_gate_equals_percentile_zero(orc):
+    xyz = _variant_cloud()
+    p = dict(k=12, beta=3.0, leaf_capacity=256)
+    off = orc.denoise(xyz, _params(orc, stage_off=2, **p), debug=True)
+    q0 = orc.denoise(xyz, _params(orc, rho_percentile=0.0, **p), debug=True)
+    assert not (off["leaf_n1"] == 1).any()              # no leaf with a single point of P_1
+    assert np.array_equal(off["stage"], q0["stage"]) and np.array_equal(off["score"], q0["score"])
+    full = orc.denoise(xyz, _params(orc, rho_percentile=10.0, **p))
+    assert (full["stage"] == 2).any() and not (off["stage"] == 2).any()
+
+
+def test_without_score_keeps_p2(orc):
+    xyz = _variant_cloud()
+    p = dict(k=12, beta=3.0)
+    off = orc.denoise(xyz, _params(orc, stage_off=4, **p))
+    lam1 = orc.denoise(xyz, _params(orc, lam=1.0, **p))                   # Top-lambda with lambda = 1 keeps P_2
+    assert np.array_equal(off["mask"], lam1["mask"]) and not off["score"].any()
+    only_a1 = orc.denoise(xyz, _params(orc, stage_off=6, **p))             # A1 alone (Table 9 "OnlyA1")
+    assert np.array_equal(only_a1["mask"], lam1["stage"] != 1) and not (only_a1["stage"] == 2).any()
+    none = orc.denoise(xyz, _params(orc, stage_off=7, **p))
+    assert none["mask"].all()
+
+
+def test_rescore_on_p2_equals_scoring_p2_alone(orc):
+    # one leaf, voxel gate passing every point: the kNN recomputed within P_2 for
+    # the score is the kNN of the cloud made of P_2 alone, scored without a gate
+    rng = np.random.default_rng(25)
+    xyz = np.concatenate([rng.normal(size=(600, 3)), rng.uniform(-4, 4, size=(40, 3))]).astype(np.float32)
+    base = dict(k=10, min_vox_count=1, leaf_capacity=4096, rho_percentile=8.0)
+    r = orc.denoise(xyz, _params(orc, rescore_p2=1, **base))
+    p2 = r["stage"] != 2
+    assert 0 < (~p2).sum() < len(xyz)
+    alone = orc.denoise(np.ascontiguousarray(xyz[p2]), _params(orc, stage_off=2, **base))
+    assert np.array_equal(r["stage"][p2], alone["stage"])
+    assert np.allclose(r["score"][p2], alone["score"], rtol=1e-12, atol=0)
+    # with nothing removed by the gate, rescoring changes nothing
+    same = dict(base, rho_percentile=0.0)
+    assert np.array_equal(orc.denoise(xyz, _params(orc, rescore_p2=1, **same))["score"],
+                          orc.denoise(xyz, _params(orc, **same))["score"])
+
+
+def test_without_octree_is_one_leaf(orc):
+    xyz = _variant_cloud()
+    p = dict(k=12, beta=3.0)
+    flat = orc.denoise(xyz, _params(orc, leaf_capacity=0xFFFFFFFF, **p), debug=True)
+    d0 = orc.denoise(xyz, _params(orc, max_depth=0, **p), debug=True)
+    assert flat["n_leaves"] == 1 and flat["leaf_count"][0] == len(xyz)
+    assert np.array_equal(flat["stage"], d0["stage"]) and np.array_equal(flat["score"], d0["score"])
