@@ -53,7 +53,8 @@ extern "C" {
 
 /*
  * Method parameters.  Every field is read on every call.  Values the paper
- * states are noted; the others are unstated there and are readings.
+ * states are noted; the others are unstated there and are readings.  The
+ * "without octree" configuration of Table 8 is leaf_capacity >= n (one leaf).
  */
 typedef struct denoise_params {
   uint32_t k;              /* K neighbours, 1..64 (paper default 12; Eq. 13, Sec. 4.3.1)        */
@@ -71,6 +72,15 @@ typedef struct denoise_params {
   float lambda;            /* Top-lambda keep ratio in (0, 1] (Sec. 3, end)                     */
   float tau;               /* log-score threshold of the THRESHOLD rule                         */
   float temperature;       /* soft-mask temperature T > 0 (differentiable form only)            */
+  uint32_t stage_off;      /* structural ablations of Sec. 4.3.2 (Table 9), 0 = the method:    */
+                           /*  bit 0 no voxel gate (A1): every point of a leaf is in P_1;      */
+                           /*  bit 1 no density gate (A2): P_2 = P_1, and a lone point of a    */
+                           /*        leaf is scored (F = 0) instead of removed;                */
+                           /*  bit 2 no score selection (A3): every point of P_2 is kept with  */
+                           /*        score 0 (with bit 1 also set, no kNN is computed)         */
+  uint32_t rescore_p2;     /* 1: the score uses a kNN recomputed within P_2 (its own k_eff,    */
+                           /*    r_K, densities and rho_med): the other reading of Eq. 21;     */
+                           /*    0 = the kNN on P_1 (Sec. 3's single N x K table)              */
 } denoise_params;
 
 typedef struct denoise_ctx denoise_ctx;

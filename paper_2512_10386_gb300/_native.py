@@ -54,6 +54,8 @@ class denoise_params(ctypes.Structure):
         ("lambda_", ctypes.c_float),
         ("tau", ctypes.c_float),
         ("temperature", ctypes.c_float),
+        ("stage_off", ctypes.c_uint32),
+        ("rescore_p2", ctypes.c_uint32),
     ]
 
 

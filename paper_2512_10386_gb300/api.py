@@ -39,11 +39,14 @@ class Params:
     lam: float = 0.95
     tau: float = 0.0
     temperature: float = 0.05
+    stage_off: int = 0      # ablations (Table 9): bit 0 no voxel gate, bit 1 no density gate, bit 2 no score
+    rescore_p2: int = 0     # 1: the score uses a kNN recomputed within P_2
 
     def to_c(self) -> N.denoise_params:
         return N.denoise_params(self.k, self.leaf_capacity, self.max_depth, self.beta, self.min_vox_count,
                                 self.rho_percentile, self.alpha, self.sigma, self.gamma, self.eps_rho,
-                                self.eps_k, self.select_mode, self.lam, self.tau, self.temperature)
+                                self.eps_k, self.select_mode, self.lam, self.tau, self.temperature,
+                                self.stage_off, self.rescore_p2)
 
 
 @dataclasses.dataclass

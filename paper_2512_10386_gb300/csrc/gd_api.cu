@@ -124,6 +124,7 @@ int check_params(const denoise_params *p) {
   if (!isfinite(p->eps_rho) || !isfinite(p->eps_k) || !isfinite(p->tau)) return DENOISE_E_INVAL;
   if (p->select_mode > 1) return DENOISE_E_INVAL;
   if (!(p->temperature > 0.0f) || !isfinite(p->temperature)) return DENOISE_E_INVAL;
+  if (p->stage_off > 7u || p->rescore_p2 > 1u) return DENOISE_E_INVAL;
   return DENOISE_OK;
 }
 

@@ -441,9 +441,12 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     S.delta = A.frames[lf.frame].delta;
     S.run = 0;
   }
+  // structural variants (Sec. 4.3.2): stages switched off (A1 voxel gate, A2
+  // density gate, A3 score selection) and the score on a kNN within P_2
+  const bool a1_on = !(P.stage_off & 1u), a2_on = !(P.stage_off & 2u), a3_on = !(P.stage_off & 4u);
   // ---- Eq. 12: voxel occupancy (hash with warp-aggregated atomics)
   const uint32_t hcap = pow2ceil(2 * nt);  // <= the carved capacity
-  for (uint32_t i = tid; i < hcap; i += NT) {
+  for (uint32_t i = tid; i < hcap && a1_on; i += NT) {
     M.hkey[i] = kEmpty;
     M.hcnt[i] = 0;
   }
@@ -451,7 +454,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   const float lo0 = S.lo[0], lo1 = S.lo[1], lo2 = S.lo[2], h = S.h;
   // each point's hash slot, for the gate below (wa is idle until the score weights)
   uint32_t *const vslot = reinterpret_cast<uint32_t *>(M.wa);
-  for (uint32_t base = 0; base < nt; base += NT) {
+  for (uint32_t base = 0; base < nt && a1_on; base += NT) {
     const uint32_t i = base + tid;
     unsigned long long key = kInvalid;
     if (i < nt) {
@@ -483,8 +486,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         atomicOr(&A.ctr->status, kStInternal);
         g = 0;
       }
-      const uint32_t c = M.hcnt[vslot[i]];
-      in1 = c >= P.min_vox_count;
+      const uint32_t c = a1_on ? M.hcnt[vslot[i]] : 0u;
+      in1 = !a1_on || c >= P.min_vox_count;
       if ((kRec && A.use_dbg)) {
         if (A.dbg.vox_count) A.dbg.vox_count[g] = c;
         if (A.dbg.leaf_start) A.dbg.leaf_start[g] = lf.start - fbeg;
@@ -515,22 +518,36 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     }
     __syncthreads();
   }
-  const uint32_t n1 = S.run;
+  uint32_t n1 = S.run;  // |P_1|; |P_2| once P_2 is compacted for its own kNN
   for (uint32_t u = tid; u < kPad; u += NT) {  // the NaN padding after P_1
     X[n1 + u] = __int_as_float(0x7FFFFFFF);
     Y[n1 + u] = __int_as_float(0x7FFFFFFF);
     Z[n1 + u] = __int_as_float(0x7FFFFFFF);
     W[n1 + u] = 0u;
   }
-  if (n1 <= 1) {  // no neighbour exists: the density gate cannot keep it
-    for (uint32_t i = tid; i < n1; i += NT) write_point<kRec>(A, W[i], 0, 0.0f, 2);
+  if (!a2_on && !a3_on) {  // no gate or score needs a neighbour: P_1 is kept
+    for (uint32_t i = tid; i < n1; i += NT) write_point<kRec>(A, W[i], 1, 0.0f, 0);
+    if (tid == 0) {
+      atomicAdd(&A.ctr->n_p1, (unsigned long long)n1);
+      atomicAdd(&A.ctr->n_p2, (unsigned long long)n1);
+    }
     return;
   }
-  const uint32_t keff = (P.k < n1 - 1) ? P.k : n1 - 1;
+  if (n1 <= 1) {  // no neighbour exists: the density gate cannot keep it
+    // without the density gate the lone point is scored, F = 0 (an empty sum):
+    // Top-lambda keeps ceil(lambda * 1) = 1 point, ln 0 >= tau never holds
+    const bool keep = !a2_on && P.select_mode == DENOISE_SELECT_TOPRATIO;
+    for (uint32_t i = tid; i < n1; i += NT)
+      write_point<kRec>(A, W[i], keep ? 1 : 0, 0.0f, a2_on ? 2 : (keep ? 0 : 3));
+    return;
+  }
+  uint32_t keff = (P.k < n1 - 1) ? P.k : n1 - 1;
   // the neighbour bitmap (shared-memory path): region A if it fits, else the spill area
-  uint32_t *const tbl = (bitmap_words(n1) * 4u <= M.nbr_bytes)
-                            ? reinterpret_cast<uint32_t *>(M.nbr)
-                            : reinterpret_cast<uint32_t *>(A.big_scratch + (size_t)lf.start * A.big_bpp);
+  auto bitmap_at = [&](uint32_t n) {
+    return (bitmap_words(n) * 4u <= M.nbr_bytes) ? reinterpret_cast<uint32_t *>(M.nbr)
+                                                  : reinterpret_cast<uint32_t *>(A.big_scratch + (size_t)lf.start * A.big_bpp);
+  };
+  uint32_t *tbl = bitmap_at(n1);
   if (tid == 0) {
     atomicAdd(&A.ctr->knn_pairs, (unsigned long long)n1 * (unsigned long long)(n1 - 1));
     atomicAdd(&A.ctr->n_p1, (unsigned long long)n1);
@@ -538,10 +555,14 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   if (tid == NT - 1) {  // Eq. 14 rank (FP64, one thread), taken off the later critical path
     const double pos = __dadd_rn(__ddiv_rn(__dmul_rn((double)n1, (double)P.rho_percentile), 100.0), 0.5);
     const double cc = ceil(pos);
-    S.crank = (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;
+    S.crank = !a2_on ? 1u : (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;  // rank 1: nothing removed
   }
-  const uint32_t sn = pow2ceil(n1);
+  uint32_t sn = pow2ceil(n1);
   __syncthreads();  // P_1 and its padding complete
+  uint32_t *const vbuf = reinterpret_cast<uint32_t *>(M.sbuf);
+  // one kNN on P_1, and with rescore_p2 a second one within P_2 (its own k_eff, r_K, densities)
+#pragma unroll 1
+  for (uint32_t kpass = 0;; ++kpass) {
 
   // ---- kNN on P_1 (excluding self), order (d^2, input index): one thread per query,
   // candidates broadcast from shared memory to the warp, four per 16-byte load.
@@ -554,7 +575,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   // parks B's few members, which are sorted to finish the set.  A boundary
   // bucket with more members than the buffer is counted again at 32 times the
   // resolution first.  Ties in d^2 across the cut are broken by input index.
-  {
+  if (keff > 0) {  // (a single point of P_2 has no neighbour to score with: F = 0)
     constexpr int PL = kPacked ? 11 : 21;  // count planes: counts < 2^PL (n1 - 1 candidates)
     if (!kPacked && n1 >= (1u << PL)) {     // beyond the spill path's counters: refuse, do not guess
       if (tid == 0) atomicOr(&A.ctr->status, kStInternal);
@@ -823,18 +844,76 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   }
   __syncthreads();
 
-  // ---- Eq. 14: exact percentile cut, as a rank cut on r_K^2 (rho decreasing in r_K)
-  uint32_t *const vbuf = reinterpret_cast<uint32_t *>(M.sbuf);
+  // ---- Eq. 14: exact percentile cut, as a rank cut on r_K^2 (rho decreasing in r_K);
+  // after the kNN within P_2 every point is in P_2 (the sort serves the median)
   for (uint32_t i = tid; i < sn; i += NT) vbuf[i] = (i < n1) ? __float_as_uint(M.r2[i]) : 0xFFFFFFFFu;
   __syncthreads();
   block_sort<uint32_t>(vbuf, sn, 0xFFFFFFFFu);
-  const uint32_t Rb = vbuf[n1 - S.crank];
+  const uint32_t Rb = kpass == 0 ? vbuf[n1 - S.crank] : 0xFFFFFFFFu;
   for (uint32_t i = tid; i < n1; i += NT) {
     const uint32_t v = vbuf[i];
     if (v <= Rb && (i + 1 == n1 || vbuf[i + 1] > Rb)) S.m = i + 1;
     M.flag[i] = (__float_as_uint(M.r2[i]) <= Rb) ? 1 : 0;
   }
   __syncthreads();
+  if (kpass > 0 || (a3_on && !P.rescore_p2)) break;
+  if (!a3_on) {  // no score selection: P_2 is kept with score 0
+    for (uint32_t i = tid; i < n1; i += NT) {
+      const uint8_t f = M.flag[i];
+      write_point<kRec>(A, W[i], f ? 1 : 0, 0.0f, f ? 0 : 2);
+    }
+    if (tid == 0) atomicAdd(&A.ctr->n_p2, (unsigned long long)S.m);
+    return;
+  }
+  // rescore_p2: the points the density gate removed get their results now, and
+  // P_2 is compacted in place (order kept) for its own kNN
+  if (tid == 0) S.run = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < n1; base += NT) {
+    const uint32_t i = base + tid;
+    const bool in2 = i < n1 && M.flag[i];
+    float x = 0.f, y = 0.f, z = 0.f;
+    uint32_t g = 0;
+    if (i < n1) {
+      x = X[i];
+      y = Y[i];
+      z = Z[i];
+      g = W[i];
+      if (!in2) write_point<kRec>(A, g, 0, 0.0f, 2);
+    }
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, in2);
+    if (lane == 0) S.wsum[w] = __popc(bal);
+    __syncthreads();  // every read of this round is done before the writes below
+    uint32_t off = S.run;
+    for (uint32_t ww = 0; ww < w; ++ww) off += S.wsum[ww];
+    if (in2) {
+      const uint32_t pos = off + __popc(bal & lt);  // <= i: never ahead of a later round's reads
+      X[pos] = x;
+      Y[pos] = y;
+      Z[pos] = z;
+      W[pos] = g;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t t = 0;
+      for (uint32_t ww = 0; ww < NW; ++ww) t += S.wsum[ww];
+      S.run += t;
+    }
+    __syncthreads();
+  }
+  n1 = S.run;
+  for (uint32_t u = tid; u < kPad; u += NT) {
+    X[n1 + u] = __int_as_float(0x7FFFFFFF);
+    Y[n1 + u] = __int_as_float(0x7FFFFFFF);
+    Z[n1 + u] = __int_as_float(0x7FFFFFFF);
+    W[n1 + u] = 0u;
+  }
+  keff = n1 <= 1 ? 0u : (P.k < n1 - 1) ? P.k : n1 - 1;
+  tbl = bitmap_at(n1);
+  sn = pow2ceil(n1);
+  if (tid == 0 && keff) atomicAdd(&A.ctr->knn_pairs, (unsigned long long)n1 * (unsigned long long)(n1 - 1));
+  __syncthreads();
+  }  // kpass
   const uint32_t m = S.m;
   // ---- Eq. 16: median density over P_2 and the per-leaf constants of the score.
   // With rho(r2) = k_eff / (4/3 pi r2^1.5), the score needs
