@@ -23,7 +23,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp"]
 
 OK, EINVAL, ENONFINITE, ENOMEM = 0, -1, -2, -3
 
@@ -109,6 +109,9 @@ def _load():
         lib = ctypes.CDLL(build())
         lib.orc_denoise.argtypes = [_P, ctypes.c_int64, ctypes.POINTER(_Params), ctypes.POINTER(_Out)]
         lib.orc_denoise.restype = ctypes.c_int
+        lib.orc_denoise_threads.argtypes = [_P, ctypes.c_int64, ctypes.POINTER(_Params), ctypes.POINTER(_Out),
+                                            ctypes.c_int]
+        lib.orc_denoise_threads.restype = ctypes.c_int
         lib.orc_softf1.argtypes = [_P, ctypes.c_int64, ctypes.POINTER(_Params), _P, _P, _P, _P, _P]
         lib.orc_softf1.restype = ctypes.c_int
         lib.orc_cbrt_spec.argtypes = [ctypes.c_double]
@@ -135,10 +138,11 @@ def _ptr(a):
     return None if a is None else a.ctypes.data
 
 
-def denoise(xyz, params: Params | None = None, debug: bool = False) -> dict:
+def denoise(xyz, params: Params | None = None, debug: bool = False, threads: int = 1) -> dict:
     """Run the whole method on one cloud.  Returns a dict of numpy arrays:
     mask, stage, score (input order); with ``debug`` also the per-stage
-    intermediates (keys, leaves, voxel counts, neighbour lists, ...)."""
+    intermediates (keys, leaves, voxel counts, neighbour lists, ...).
+    ``threads`` > 1 spreads the leaves over host threads (same results)."""
     params = params or Params()
     xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
     n = xyz.shape[0]
@@ -157,7 +161,7 @@ def denoise(xyz, params: Params | None = None, debug: bool = False) -> dict:
                  leaf_n1=np.zeros(nn, np.uint32), leaf_n2=np.zeros(nn, np.uint32),
                  root=np.zeros(4, np.float32))
     out = _Out(**{f: _ptr(r.get(f)) for f, _ in _Out._fields_})
-    st = _load().orc_denoise(_ptr(xyz), n, ctypes.byref(params._c()), ctypes.byref(out))
+    st = _load().orc_denoise_threads(_ptr(xyz), n, ctypes.byref(params._c()), ctypes.byref(out), int(threads))
     if st != OK:
         raise OracleError(st)
     res = {k_: v[:n] for k_, v in r.items() if k_ in ("mask", "stage", "score")}

@@ -462,7 +462,7 @@ static int check_params(const orc_params *p) {
 }
 
 static int run(const float *xyz, int64_t n, const orc_params *p, orc_out *o, double *dF,
-               double *F_all, uint8_t *stage_all) {
+               double *F_all, uint8_t *stage_all, int threads) {
   int st = check_params(p);
   if (st) return st;
   for (int64_t i = 0; i < 3 * n; ++i)
@@ -506,13 +506,20 @@ static int run(const float *xyz, int64_t n, const orc_params *p, orc_out *o, dou
 
   ctx_t c = {xyz, p, side * INV_TWO21, o, dF, F_all, stage_all};
   for (int64_t i = 0; i < n; ++i) { F_all[i] = 0.0; stage_all[i] = 0; }
+  /* The leaves are independent (each writes only its own points' entries), so
+   * with threads > 1 they are spread over threads; the arithmetic of every leaf
+   * is the same either way.  (Used only to time the oracle on all host cores.) */
+  int failed = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4) num_threads(threads > 0 ? threads : 1) if (threads > 1)
+#endif
   for (int64_t L = 0; L < tree.n_leaves; ++L) {
     if (o->leaf_start) o->leaf_start[L] = leaves[L].start;
     if (o->leaf_count) o->leaf_count[L] = leaves[L].count;
     if (o->leaf_level) o->leaf_level[L] = leaves[L].level;
-    st = process_leaf(&c, sorted, &leaves[L], (uint32_t)L);
-    if (st) break;
+    if (process_leaf(&c, sorted, &leaves[L], (uint32_t)L) != ORC_OK) failed = 1;
   }
+  if (failed) st = ORC_ENOMEM;
   /* Eq. 22: the union of the leaves' survivors, as a mask in input order */
   for (int64_t i = 0; i < n; ++i) {
     if (o->stage) o->stage[i] = stage_all[i];
@@ -525,13 +532,17 @@ static int run(const float *xyz, int64_t n, const orc_params *p, orc_out *o, dou
 }
 
 int orc_denoise(const float *xyz, int64_t n, const orc_params *p, orc_out *out) {
+  return orc_denoise_threads(xyz, n, p, out, 1);
+}
+
+int orc_denoise_threads(const float *xyz, int64_t n, const orc_params *p, orc_out *out, int threads) {
   orc_out none;
   memset(&none, 0, sizeof none);
   if (!out) out = &none;
   double *F = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   uint8_t *stg = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
   if (!F || !stg) return ORC_ENOMEM;
-  int st = run(xyz, n, p, out, NULL, F, stg);
+  int st = run(xyz, n, p, out, NULL, F, stg, threads);
   free(F);
   free(stg);
   return st;
@@ -551,7 +562,7 @@ int orc_softf1(const float *xyz, int64_t n, const orc_params *p, const uint8_t *
   if (!F || !dF || !rm || !dm || !stg) return ORC_ENOMEM;
   orc_params q = *p;
   q.select_mode = 1;
-  int st = run(xyz, n, &q, &none, dF, F, stg);
+  int st = run(xyz, n, &q, &none, dF, F, stg, 1);
   if (st) return st;
   const double T = p->temperature, tau = p->tau;
   double Sr = 0.0, Sy = 0.0, Sry = 0.0;

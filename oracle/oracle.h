@@ -71,6 +71,9 @@ typedef struct {
 
 /* Full pipeline (octree -> voxel gate -> kNN + density gate -> score -> select). */
 int orc_denoise(const float *xyz, int64_t n, const orc_params *p, orc_out *out);
+/* The same, with the (independent) leaves spread over `threads` host threads
+ * when the library is built with OpenMP: for timing the oracle on all cores. */
+int orc_denoise_threads(const float *xyz, int64_t n, const orc_params *p, orc_out *out, int threads);
 
 /* Soft-F1 loss of the differentiable form and its gradient with respect to
  * (alpha, sigma, gamma, tau).  noise[i] = 1 marks a noise point; in_loss (may

@@ -22,7 +22,7 @@ import collections
 import dataclasses
 import statistics
 import time
-from typing import Callable, Dict, List, Optional, Sequence
+from typing import Callable, Dict, Iterable, List, Optional, Sequence
 
 import numpy as np
 
@@ -93,7 +93,7 @@ class _Slot:
     def done(self) -> bool:
         return self.batch is not None and self.event.query()
 
-    def collect(self, t_done: float) -> List[Completion]:
+    def collect(self, t_done: float, keep_results: bool = True) -> List[Completion]:
         from . import _native as N
         st = self.den.status(self.stream)
         if st != N.DENOISE_OK:
@@ -101,9 +101,10 @@ class _Slot:
         out = []
         for i, r in enumerate(self.batch):
             a, b = self.offsets[i], self.offsets[i + 1]
+            res = ((self.mask[a:b].numpy().copy(), self.score[a:b].numpy().copy(), self.stage[a:b].numpy().copy())
+                   if keep_results else (None, None, None))
             out.append(Completion(r.rid, r.kind, b - a, r.t_arrival, self.t_admit, t_done, self.index,
-                                  len(self.batch), self.mask[a:b].numpy().copy(), self.score[a:b].numpy().copy(),
-                                  self.stage[a:b].numpy().copy()))
+                                  len(self.batch), *res))
         self.batch = None
         return out
 
@@ -164,27 +165,34 @@ class Server:
         for s in self.slots:
             s.close()
 
-    def serve(self, requests: Sequence[Request], realtime: bool = True, clock: Callable[[], float] = time.perf_counter,
-              idle_sleep: float = 2e-4) -> List[Completion]:
-        """Play `requests` (sorted by t_arrival) through the server.  With
+    def serve(self, requests: Iterable[Request], realtime: bool = True, clock: Callable[[], float] = time.perf_counter,
+              idle_sleep: float = 2e-4, keep_results: bool = True) -> List[Completion]:
+        """Play `requests` (in arrival order) through the server.  With
         realtime=True a request becomes visible at its arrival time; otherwise
-        all are visible at once (throughput mode, arrival = start)."""
-        pending = collections.deque(sorted(requests, key=lambda r: r.t_arrival))
+        all are visible at once (throughput mode, arrival = start).  `requests`
+        may be a list or a lazy iterator (each request is drawn when its arrival
+        time comes, so a long stream need not be held in memory); with
+        keep_results=False the completions carry no per-point arrays."""
+        if isinstance(requests, (list, tuple)):
+            requests = sorted(requests, key=lambda r: r.t_arrival)
+        source = iter(requests)
+        nxt = next(source, None)
         queue: collections.deque = collections.deque()
         done: List[Completion] = []
         t0 = clock()
-        if not realtime:
-            for r in pending:
-                r.t_arrival = 0.0
-        total = len(pending)
-        while len(done) < total:
+        while nxt is not None or queue or any(s.batch is not None for s in self.slots):
             now = clock() - t0
-            while pending and pending[0].t_arrival <= now:
-                queue.append(pending.popleft())
+            while nxt is not None and (not realtime or nxt.t_arrival <= now):
+                if not realtime:
+                    nxt.t_arrival = 0.0
+                queue.append(nxt)
+                nxt = next(source, None)
+                if not realtime and len(queue) >= 4 * len(self.slots) * self.sched.max_frames:
+                    break                                    # throughput mode: a bounded look-ahead
             progressed = False
             for s in self.slots:
                 if s.done():
-                    comps = s.collect(clock() - t0)
+                    comps = s.collect(clock() - t0, keep_results)
                     self.sched.release(sum(c.n for c in comps))
                     done.extend(comps)
                     progressed = True
@@ -199,8 +207,8 @@ class Server:
                 time.sleep(idle_sleep)                       # work in flight: poll again soon
             elif queue:
                 raise RuntimeError(f"request {queue[0].rid} cannot be admitted (point budget too small)")
-            elif pending:
-                time.sleep(min(max(pending[0].t_arrival - (clock() - t0), 0.0), 0.01))
+            elif nxt is not None:
+                time.sleep(min(max(nxt.t_arrival - (clock() - t0), 0.0), 0.01))
         return sorted(done, key=lambda c: c.rid)
 
 

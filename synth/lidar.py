@@ -205,7 +205,7 @@ class serving_stream:
     """
 
     def __init__(self, seed: int = 7, n_frames: int = 2000, rate_hz: float = 20.0,
-                 dense_points: int = 1_000_000, sparse_points: int = 100_000, pool: int = 2):
+                 dense_points: int = 1_000_000, sparse_points: int = 100_000, pool: int = 2, bases=None):
         rng = np.random.default_rng(seed)
         gaps = rng.exponential(1.0 / rate_hz, n_frames)
         kinds = np.where(rng.uniform(size=n_frames) < 0.5, "dense", "sparse")
@@ -214,7 +214,15 @@ class serving_stream:
         self.seed = seed
         self.pool = pool
         self.sizes = {"dense": dense_points, "sparse": sparse_points}
-        self._base = {}
+        self._base = dict(bases or {})
+
+    def bases(self) -> dict:
+        """The ray-cast base scenes of the pool (built on first use); pass them to
+        another ``serving_stream`` of the same seed (``bases=``) to skip the ray casting."""
+        for kind in ("dense", "sparse"):
+            for slot in range(self.pool):
+                self._base_frame(kind, slot)
+        return dict(self._base)
 
     def _base_frame(self, kind, slot):
         key = (kind, slot)
