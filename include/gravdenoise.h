@@ -239,6 +239,7 @@ typedef struct denoise_stats {
   uint64_t knn_pairs;    /* sum over leaves of |P_1|(|P_1|-1): candidate pairs scanned */
   uint64_t n_p1;         /* points that passed the voxel gate                         */
   uint64_t n_p2;         /* points that passed the density gate                       */
+  uint64_t score_terms;  /* neighbour terms summed by the score, sum over P_2 of k_eff  */
   uint32_t launches;     /* kernels launched by the call                              */
   uint32_t n_stages;     /* entries valid in stage_ms                                 */
   float stage_ms[8];     /* with profiling: init+bbox+keys, sort, leaf finder, leaf prep, fused leaf kernel */

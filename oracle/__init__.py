@@ -57,6 +57,7 @@ class _Params(ctypes.Structure):
         ("temperature", ctypes.c_float),
         ("stage_off", ctypes.c_uint32),
         ("rescore_p2", ctypes.c_uint32),
+        ("cross_leaf", ctypes.c_uint32),
     ]
 
 
@@ -92,12 +93,13 @@ class Params:
     temperature: float = 0.05
     stage_off: int = 0      # ablations: bit 0 no voxel gate (A1), bit 1 no density gate (A2), bit 2 no score (A3)
     rescore_p2: int = 0     # 1: the score uses a kNN recomputed within P_2
+    cross_leaf: int = 0     # 1: kNN candidates from the 27 same-level octree cells around the leaf
 
     def _c(self) -> _Params:
         return _Params(self.k, self.leaf_capacity, self.max_depth, self.beta, self.min_vox_count,
                        self.rho_percentile, self.alpha, self.sigma, self.gamma, self.eps_rho,
                        self.eps_k, self.select_mode, self.lam, self.tau, self.temperature,
-                       self.stage_off, self.rescore_p2)
+                       self.stage_off, self.rescore_p2, self.cross_leaf)
 
 
 _lib = None

@@ -244,16 +244,18 @@ static int knn_list(ctx_t *c, const uint32_t *pts, uint32_t n1, uint32_t keff, u
  *                   k_eff, r_K and densities, and rho_med over them) instead of
  *                   the kNN on P_1 (the other reading of Eq. 21).
  * "Without octree" (Table 8) is leaf_capacity >= N: the root is the only leaf. */
-static int process_leaf(ctx_t *c, const keyed_t *sorted, const leaf_t *lf, uint32_t leaf_id) {
+/* Eq. 10-12 for one leaf: extents, voxel size h, voxel occupancy and the voxel
+ * gate.  p1 [count] receives P_1 (input indices, leaf order); returns |P_1|, or
+ * -1 when out of memory. */
+static int64_t voxel_gate(ctx_t *c, const keyed_t *sorted, const leaf_t *lf, uint32_t leaf_id, uint32_t *p1) {
   const orc_params *p = c->p;
   orc_out *o = c->out;
-  const int a1_on = !(p->stage_off & 1u), a2_on = !(p->stage_off & 2u), a3_on = !(p->stage_off & 4u);
+  const int a1_on = !(p->stage_off & 1u);
   const uint32_t nt = lf->count;
   uint32_t *idx = (uint32_t *)malloc(sizeof(uint32_t) * nt);
   uint32_t *vox = (uint32_t *)malloc(sizeof(uint32_t) * nt * 3);
   uint32_t *cnt = (uint32_t *)malloc(sizeof(uint32_t) * nt);
-  uint32_t *p1 = (uint32_t *)malloc(sizeof(uint32_t) * nt);
-  if (!idx || !vox || !cnt || !p1) return ORC_ENOMEM;
+  if (!idx || !vox || !cnt) return -1;
   for (uint32_t t = 0; t < nt; ++t) idx[t] = sorted[lf->start + t].idx;
 
   /* Eq. 10 with R3: leaf bounding box, extents floored at delta */
@@ -305,6 +307,21 @@ static int process_leaf(ctx_t *c, const keyed_t *sorted, const leaf_t *lf, uint3
   if (o->leaf_n1) o->leaf_n1[leaf_id] = n1;
   if (o->leaf_n2) o->leaf_n2[leaf_id] = 0;
   if (o->leaf_rho_med) o->leaf_rho_med[leaf_id] = 0.0;
+
+  free(idx); free(vox); free(cnt);
+  return n1;
+}
+
+static int process_leaf(ctx_t *c, const keyed_t *sorted, const leaf_t *lf, uint32_t leaf_id) {
+  const orc_params *p = c->p;
+  orc_out *o = c->out;
+  const int a2_on = !(p->stage_off & 2u), a3_on = !(p->stage_off & 4u);
+  uint32_t *p1 = (uint32_t *)malloc(sizeof(uint32_t) * lf->count);
+  if (!p1) return ORC_ENOMEM;
+  const int64_t g1 = voxel_gate(c, sorted, lf, leaf_id, p1);
+  if (g1 < 0) return ORC_ENOMEM;
+  const uint32_t n1 = (uint32_t)g1;
+  uint32_t *idx = NULL, *vox = NULL, *cnt = NULL;  /* (kept by voxel_gate) */
 
   if (!a2_on && !a3_on) {  /* neither gate nor score needs a neighbour: P_1 is kept */
     if (o->leaf_n2) o->leaf_n2[leaf_id] = n1;
@@ -444,6 +461,174 @@ static int process_leaf(ctx_t *c, const keyed_t *sorted, const leaf_t *lf, uint3
   return ORC_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* R14: cross-leaf kNN.  The candidates of the points of a leaf at level L */
+/* are the P_1 points of the 27 octree cells of level L around (and       */
+/* including) the leaf's own cell: neighbours come from adjacent cells    */
+/* too, so a point near a leaf's border is not cut off from the points    */
+/* across it.  Densities are per point (each from its own kNN); the       */
+/* percentile gate, the median and the selection stay per leaf, and the   */
+/* score of a point uses its neighbours' own densities with the rho_med   */
+/* of the point's leaf.                                                   */
+/* ------------------------------------------------------------------ */
+static uint32_t deinterleave(uint64_t key, int axis) {  /* axis 0: x (bit 3b+2), 1: y, 2: z */
+  uint32_t q = 0;
+  for (int b = 0; b < 21; ++b) q |= (uint32_t)((key >> (3 * b + 2 - axis)) & 1u) << b;
+  return q;
+}
+
+static int64_t lower_key(const keyed_t *sorted, int64_t n, uint64_t key) {  /* first position with key >= key */
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (sorted[mid].key < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+static int run_cross_leaf(ctx_t *c, const keyed_t *sorted, int64_t n, const leaf_t *leaves, int64_t n_leaves) {
+  const orc_params *p = c->p;
+  orc_out *o = c->out;
+  uint8_t *in1 = (uint8_t *)calloc((size_t)n, 1);           /* by input index */
+  uint32_t *leaf_of = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+  uint32_t *lp1 = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+  uint32_t *keff_of = (uint32_t *)calloc((size_t)n, sizeof(uint32_t));
+  uint32_t *nbi = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n * p->k); /* neighbour input indices */
+  float *nd2 = (float *)malloc(sizeof(float) * (size_t)n * p->k);
+  float *r2 = (float *)calloc((size_t)n, sizeof(float));
+  double *rho = (double *)calloc((size_t)n, sizeof(double));
+  uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+  cand_t *cl = (cand_t *)malloc(sizeof(cand_t) * (size_t)n);
+  if (!in1 || !leaf_of || !lp1 || !keff_of || !nbi || !nd2 || !r2 || !rho || !cand || !cl) return ORC_ENOMEM;
+  /* Eq. 10-12 per leaf: P_1 */
+  for (int64_t L = 0; L < n_leaves; ++L) {
+    const int64_t g1 = voxel_gate(c, sorted, &leaves[L], (uint32_t)L, lp1);
+    if (g1 < 0) return ORC_ENOMEM;
+    for (int64_t t = 0; t < g1; ++t) in1[lp1[t]] = 1;
+    for (uint32_t t = 0; t < leaves[L].count; ++t) leaf_of[sorted[leaves[L].start + t].idx] = (uint32_t)L;
+  }
+  const float delta2 = c->delta * c->delta;
+  /* the kNN of every P_1 point among the P_1 points of its leaf's 27-cell block */
+  for (int64_t L = 0; L < n_leaves; ++L) {
+    const leaf_t *lf = &leaves[L];
+    const uint32_t lv = lf->level;
+    const int sh = 3 * (21 - (int)lv);
+    const uint64_t k0 = sorted[lf->start].key;
+    const int64_t cx = deinterleave(k0, 0) >> (21 - lv), cy = deinterleave(k0, 1) >> (21 - lv),
+                  cz = deinterleave(k0, 2) >> (21 - lv);
+    const int64_t side = (int64_t)1 << lv;
+    uint32_t nc = 0;
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dz = -1; dz <= 1; ++dz) {
+          const int64_t x = cx + dx, y = cy + dy, z = cz + dz;
+          if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) continue;
+          const uint64_t pre = orc_interleave((uint32_t)x, (uint32_t)y, (uint32_t)z);  /* level-lv cell */
+          const uint64_t kb = (sh >= 64) ? 0 : pre << sh, ke = (sh >= 64) ? ~0ull : (pre + 1) << sh;
+          int64_t a = lower_key(sorted, n, kb);
+          const int64_t b = (lv == 0) ? n : lower_key(sorted, n, ke);
+          for (; a < b; ++a)
+            if (in1[sorted[a].idx]) cand[nc++] = sorted[a].idx;
+        }
+    for (uint32_t t = 0; t < lf->count; ++t) {
+      const uint32_t i = sorted[lf->start + t].idx;
+      if (!in1[i] || nc <= 1) continue;
+      const uint32_t keff = (p->k < nc - 1) ? p->k : nc - 1;
+      uint32_t m = 0;
+      for (uint32_t u = 0; u < nc; ++u) {
+        if (cand[u] == i) continue;
+        cl[m].d2 = sq_dist(c, i, cand[u]);
+        cl[m].idx = cand[u];
+        cl[m].pos = u;
+        ++m;
+      }
+      qsort(cl, m, sizeof(cand_t), cmp_cand);
+      for (uint32_t s2 = 0; s2 < keff; ++s2) {
+        nbi[(size_t)i * p->k + s2] = cl[s2].idx;
+        nd2[(size_t)i * p->k + s2] = cl[s2].d2;
+      }
+      keff_of[i] = keff;
+      float rk2 = cl[keff - 1].d2;
+      r2[i] = (rk2 < delta2) ? delta2 : rk2;
+      double rr = (double)r2[i];
+      rho[i] = (double)keff / ((4.0 / 3.0) * PI_D * (rr * sqrt(rr)));  /* Eq. 13 */
+      if (o->r2) o->r2[i] = r2[i];
+      if (o->rho) o->rho[i] = rho[i];
+      if (o->nbr)
+        for (uint32_t s2 = 0; s2 < p->k; ++s2) o->nbr[(size_t)i * p->k + s2] = (s2 < keff) ? cl[s2].idx : NONE32;
+      if (o->nbr_d2)
+        for (uint32_t s2 = 0; s2 < p->k; ++s2) o->nbr_d2[(size_t)i * p->k + s2] = (s2 < keff) ? cl[s2].d2 : 0.0f;
+    }
+  }
+  /* per leaf: Eq. 14 gate, Eq. 16 median, Eq. 15-21 score, selection */
+  double *srt = (double *)malloc(sizeof(double) * (size_t)n);
+  ranked_t *rk = (ranked_t *)malloc(sizeof(ranked_t) * (size_t)n);
+  if (!srt || !rk) return ORC_ENOMEM;
+  for (int64_t L = 0; L < n_leaves; ++L) {
+    const leaf_t *lf = &leaves[L];
+    uint32_t n1 = 0;
+    for (uint32_t t = 0; t < lf->count; ++t) {
+      const uint32_t i = sorted[lf->start + t].idx;
+      if (!in1[i]) continue;
+      if (!keff_of[i]) { c->stage_all[i] = 2; continue; }  /* no candidate besides itself */
+      lp1[n1++] = i;
+    }
+    if (o->leaf_n2) o->leaf_n2[L] = 0;
+    if (o->leaf_rho_med) o->leaf_rho_med[L] = 0.0;
+    if (!n1) continue;
+    for (uint32_t a = 0; a < n1; ++a) srt[a] = rho[lp1[a]];
+    qsort(srt, n1, sizeof(double), cmp_double);
+    double pos = (double)n1 * (double)p->rho_percentile / 100.0 + 0.5;
+    double cc = ceil(pos);
+    uint32_t crank = (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;
+    double thr = srt[crank - 1];
+    uint32_t m2 = 0;
+    for (uint32_t a = 0; a < n1; ++a) {
+      if (rho[lp1[a]] >= thr) {  /* P_2, compacted in place (m2 <= a) */
+        srt[m2] = rho[lp1[a]];
+        lp1[m2] = lp1[a];
+        ++m2;
+      } else {
+        c->stage_all[lp1[a]] = 2;
+      }
+    }
+    qsort(srt, m2, sizeof(double), cmp_double);
+    double rho_med = (m2 & 1u) ? srt[(m2 - 1) / 2] : 0.5 * (srt[m2 / 2 - 1] + srt[m2 / 2]);
+    if (o->leaf_rho_med) o->leaf_rho_med[L] = rho_med;
+    if (o->leaf_n2) o->leaf_n2[L] = m2;
+    const double alpha = p->alpha, sigma = p->sigma, gamma = p->gamma;
+    const double wden_den = rho_med * rho_med + p->eps_rho, eps_k = p->eps_k;
+    for (uint32_t a = 0; a < m2; ++a) {
+      const uint32_t i = lp1[a];
+      double F = 0.0;
+      const double r2i = (double)r2[i];
+      for (uint32_t s2 = 0; s2 < keff_of[i]; ++s2) {
+        const uint32_t j = nbi[(size_t)i * p->k + s2];
+        const double d2 = (double)nd2[(size_t)i * p->k + s2];
+        const double W = rho[i] * rho[j] / wden_den;                          /* Eq. 17 base */
+        const double kern = 1.0 / (pow(d2, gamma / 2.0) + eps_k);             /* Eq. 20      */
+        F += pow(W, alpha / 2.0) * exp(-d2 / (2.0 * (sigma * sigma) * r2i)) * kern;  /* Eq. 15-21 */
+      }
+      c->F_all[i] = F;
+      rk[a].f = F;
+      rk[a].idx = i;
+      rk[a].pos = a;
+    }
+    if (p->select_mode == 0) {
+      qsort(rk, m2, sizeof(ranked_t), cmp_ranked);
+      double want = ceil((double)p->lambda * (double)m2);
+      uint32_t keep = (want > (double)m2) ? m2 : (uint32_t)want;
+      for (uint32_t t = 0; t < m2; ++t) c->stage_all[rk[t].idx] = (t < keep) ? 0 : 3;
+    } else {
+      for (uint32_t t = 0; t < m2; ++t) c->stage_all[rk[t].idx] = (log(rk[t].f) >= (double)p->tau) ? 0 : 3;
+    }
+  }
+  free(srt); free(rk);
+  free(in1); free(leaf_of); free(lp1); free(keff_of); free(nbi); free(nd2); free(r2); free(rho); free(cand); free(cl);
+  return ORC_OK;
+}
+
 static int check_params(const orc_params *p) {
   if (!p) return ORC_EINVAL;
   if (p->k == 0 || p->k > 64) return ORC_EINVAL;
@@ -457,7 +642,8 @@ static int check_params(const orc_params *p) {
   if (!isfinite(p->alpha) || !(p->eps_rho >= 0.0f) || !(p->eps_k >= 0.0f)) return ORC_EINVAL;
   if (p->select_mode > 1) return ORC_EINVAL;
   if (!(p->temperature > 0.0f)) return ORC_EINVAL;
-  if (p->stage_off > 7u || p->rescore_p2 > 1u) return ORC_EINVAL;
+  if (p->stage_off > 7u || p->rescore_p2 > 1u || p->cross_leaf > 1u) return ORC_EINVAL;
+  if (p->cross_leaf && (p->stage_off || p->rescore_p2)) return ORC_EINVAL;  /* not combined (R14) */
   return ORC_OK;
 }
 
@@ -509,7 +695,16 @@ static int run(const float *xyz, int64_t n, const orc_params *p, orc_out *o, dou
   /* The leaves are independent (each writes only its own points' entries), so
    * with threads > 1 they are spread over threads; the arithmetic of every leaf
    * is the same either way.  (Used only to time the oracle on all host cores.) */
+  if (p->cross_leaf) {  /* R14 */
+    for (int64_t L = 0; L < tree.n_leaves; ++L) {
+      if (o->leaf_start) o->leaf_start[L] = leaves[L].start;
+      if (o->leaf_count) o->leaf_count[L] = leaves[L].count;
+      if (o->leaf_level) o->leaf_level[L] = leaves[L].level;
+    }
+    st = run_cross_leaf(&c, sorted, n, leaves, tree.n_leaves);
+  }
   int failed = 0;
+  if (!p->cross_leaf) {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 4) num_threads(threads > 0 ? threads : 1) if (threads > 1)
 #endif
@@ -518,6 +713,7 @@ static int run(const float *xyz, int64_t n, const orc_params *p, orc_out *o, dou
     if (o->leaf_count) o->leaf_count[L] = leaves[L].count;
     if (o->leaf_level) o->leaf_level[L] = leaves[L].level;
     if (process_leaf(&c, sorted, &leaves[L], (uint32_t)L) != ORC_OK) failed = 1;
+  }
   }
   if (failed) st = ORC_ENOMEM;
   /* Eq. 22: the union of the leaves' survivors, as a mask in input order */

@@ -37,6 +37,7 @@ typedef struct {
   uint32_t stage_off;      /* ablations (Table 9): bit 0 no voxel gate (A1), bit 1 no density
                               gate (A2), bit 2 no score selection (A3); 0 = the method         */
   uint32_t rescore_p2;     /* 1: the score uses a kNN recomputed within P_2               */
+  uint32_t cross_leaf;     /* 1: kNN candidates from the 27 same-level cells around the leaf */
 } orc_params;
 
 /* Outputs; every pointer may be NULL.  Per-point arrays are in input order. */

@@ -66,6 +66,7 @@ class denoise_stats(ctypes.Structure):
         ("knn_pairs", ctypes.c_uint64),
         ("n_p1", ctypes.c_uint64),
         ("n_p2", ctypes.c_uint64),
+        ("score_terms", ctypes.c_uint64),
         ("launches", ctypes.c_uint32),
         ("n_stages", ctypes.c_uint32),
         ("stage_ms", ctypes.c_float * 8),

@@ -223,7 +223,8 @@ class Denoiser:
     def stats(self) -> dict:
         s = N.denoise_get_stats(self.ctx)
         return {"n_points": s.n_points, "n_leaves": s.n_leaves, "knn_pairs": s.knn_pairs, "n_p1": s.n_p1,
-                "n_p2": s.n_p2, "launches": s.launches, "stage_ms": [s.stage_ms[i] for i in range(s.n_stages)]}
+                "n_p2": s.n_p2, "score_terms": s.score_terms, "launches": s.launches,
+                "stage_ms": [s.stage_ms[i] for i in range(s.n_stages)]}
 
     # -- differentiable form ---------------------------------------------------
     def soft_removal(self, n: int, stream=None) -> torch.Tensor:

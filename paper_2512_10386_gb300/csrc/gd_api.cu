@@ -676,6 +676,7 @@ int denoise_get_stats(denoise_ctx *ctx, denoise_stats *out) {
   out->knn_pairs = ctx->h_ctr->knn_pairs;
   out->n_p1 = ctx->h_ctr->n_p1;
   out->n_p2 = ctx->h_ctr->n_p2;
+  out->score_terms = ctx->h_ctr->score_terms;
   out->launches = (uint32_t)ctx->last_launches;
   out->n_stages = (uint32_t)ctx->n_stage_ms;
   for (int i = 0; i < ctx->n_stage_ms && i < 8; ++i) out->stage_ms[i] = ctx->stage_ms[i];

@@ -85,6 +85,7 @@ struct Counters {
   unsigned long long knn_pairs;
   unsigned long long n_p1;
   unsigned long long n_p2;
+  unsigned long long score_terms;        // neighbour terms summed by the score (Eq. 21)
 };
 
 // Train-mode cache written by the forward for the backward.

@@ -30,6 +30,7 @@ __global__ void k_init(FrameInfo *frames, uint32_t nframes, Counters *ctr, uint3
     ctr->knn_pairs = 0;
     ctr->n_p1 = 0;
     ctr->n_p2 = 0;
+    ctr->score_terms = 0;
   }
   for (uint32_t f = tid; f < nframes; f += stride) {
     for (int a = 0; a < 3; ++a) {

@@ -929,6 +929,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     S.keep_n = (uint32_t)ceil((double)P.lambda * (double)m);
     if (S.keep_n > m) S.keep_n = m;
     atomicAdd(&A.ctr->n_p2, (unsigned long long)m);
+    atomicAdd(&A.ctr->score_terms, (unsigned long long)m * keff);
     if ((kRec && A.use_dbg) && A.dbg.leaf_rho_med) {  // exact FP64 value for the parity output only
       const double k43pi = (4.0 / 3.0) * 3.14159265358979323846;
       auto rho_of = [&](float r2) {

@@ -58,6 +58,11 @@ MUTATIONS = [
     ("variant: voxel gate never switched off", "    if (!a1_on) {  /* the voxel gate is off", "    if (0) {  /* the voxel gate is off"),
     ("variant: score selection never switched off", "  if (!a3_on) {  /* no score selection", "  if (0) {  /* no score selection"),
     ("variant: rescoring ignored", "  if (p->rescore_p2) {", "  if (0) {"),
+    ("cross-leaf: own cell only", "    for (int dx = -1; dx <= 1; ++dx)\n      for (int dy = -1; dy <= 1; ++dy)\n        for (int dz = -1; dz <= 1; ++dz) {",
+     "    for (int dx = 0; dx <= 0; ++dx)\n      for (int dy = 0; dy <= 0; ++dy)\n        for (int dz = 0; dz <= 0; ++dz) {"),
+    ("cross-leaf: score exponent alpha", "F += pow(W, alpha / 2.0) * exp(", "F += pow(W, alpha) * exp("),
+    ("cross-leaf: eps_k dropped", "const double kern = 1.0 / (pow(d2, gamma / 2.0) + eps_k);",
+     "const double kern = 1.0 / (pow(d2, gamma / 2.0));"),
     ("voxel origin shifted", "float d = coord(c, idx[t], a) - lo[a];", "float d = coord(c, idx[t], a) - lo[a] + h * 0.5f;"),
 ]
 

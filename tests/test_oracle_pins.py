@@ -758,3 +758,41 @@ def test_without_octree_is_one_leaf(orc):
     d0 = orc.denoise(xyz, _params(orc, max_depth=0, **p), debug=True)
     assert flat["n_leaves"] == 1 and flat["leaf_count"][0] == len(xyz)
     assert np.array_equal(flat["stage"], d0["stage"]) and np.array_equal(flat["score"], d0["score"])
+
+
+# --------------------------------------------------------------------------
+# cross-leaf kNN (reading R14): candidates from the 27 same-level cells around a leaf
+# --------------------------------------------------------------------------
+def test_cross_leaf_equals_global_knn_when_cells_hold_the_neighbourhood(orc):
+    # a jittered 16^3 lattice cut into 4^3-point leaves: every point's 8 nearest lie
+    # within one lattice spacing and a half, inside the 27 cells around its leaf, so
+    # the cross-leaf kNN is the global kNN (full sort over the whole cloud) -- which
+    # the leaf-local kNN is not, for the points on a leaf's border
+    rng = np.random.default_rng(26)
+    g = np.arange(16, dtype=np.float64)
+    xyz = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    xyz = (xyz + rng.uniform(-0.2, 0.2, size=xyz.shape)).astype(np.float32)
+    p = dict(k=8, min_vox_count=1, leaf_capacity=64, rho_percentile=0.0)
+    r = orc.denoise(xyz, _params(orc, cross_leaf=1, **p), debug=True)
+    assert r["n_leaves"] == 64
+    d2 = ((xyz[:, None, :].astype(np.float64) - xyz[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(d2, np.inf)
+    want = np.argsort(d2, axis=1, kind="stable")[:, :8]
+    assert all(set(a) == set(b) for a, b in zip(r["nbr"], want))
+    local = orc.denoise(xyz, _params(orc, **p), debug=True)
+    assert sum(set(a) != set(b) for a, b in zip(local["nbr"], want)) > 500
+
+
+def test_cross_leaf_equals_leaf_local_for_a_single_leaf(orc):
+    # with the root as the only leaf the 27-cell block is the root cell: nothing changes
+    from synth import object_cloud
+    xyz, _ = object_cloud(seed=27, n_surface=2500)
+    for kw in (dict(max_depth=0), dict(leaf_capacity=0xFFFFFFFF)):
+        p = dict(k=12, beta=3.0, rho_percentile=5.0, **kw)
+        a = orc.denoise(xyz, _params(orc, **p))
+        b = orc.denoise(xyz, _params(orc, cross_leaf=1, **p))
+        assert np.array_equal(a["stage"], b["stage"]) and np.array_equal(a["score"], b["score"])
+        for mode in (dict(select_mode=1, tau=4.0),):
+            a = orc.denoise(xyz, _params(orc, **p, **mode))
+            b = orc.denoise(xyz, _params(orc, cross_leaf=1, **p, **mode))
+            assert np.array_equal(a["stage"], b["stage"])
