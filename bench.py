@@ -189,7 +189,7 @@ def _oracle_params(P=None):
                          min_vox_count=p.min_vox_count, rho_percentile=p.rho_percentile, alpha=p.alpha,
                          sigma=p.sigma, gamma=p.gamma, eps_rho=p.eps_rho, eps_k=p.eps_k,
                          select_mode=p.select_mode, lam=p.lam, tau=p.tau, temperature=p.temperature,
-                         stage_off=p.stage_off, rescore_p2=p.rescore_p2)
+                         stage_off=p.stage_off, rescore_p2=p.rescore_p2, cross_leaf=p.cross_leaf)
 
 
 def cpu_baseline_full(xyz):

@@ -81,6 +81,11 @@ typedef struct denoise_params {
   uint32_t rescore_p2;     /* 1: the score uses a kNN recomputed within P_2 (its own k_eff,    */
                            /*    r_K, densities and rho_med): the other reading of Eq. 21;     */
                            /*    0 = the kNN on P_1 (Sec. 3's single N x K table)              */
+  uint32_t cross_leaf;     /* 1: kNN candidates are the P_1 points of the 27 octree cells of   */
+                           /*    the leaf's level around the leaf's cell, not the leaf alone;  */
+                           /*    the gates, median and selection stay per leaf.  Needs        */
+                           /*    denoise_set_cross_leaf(ctx, 1); not combined with stage_off  */
+                           /*    or rescore_p2.  0 = within the leaf (Sec. 3)                  */
 } denoise_params;
 
 typedef struct denoise_ctx denoise_ctx;
@@ -283,6 +288,16 @@ int denoise_run_debug(denoise_ctx *ctx, const float *xyz, size_t n, const denois
  * Errors: E_STATE if the last forward did not run with training enabled.
  */
 int denoise_set_training(denoise_ctx *ctx, int enable);  /* default 0 */
+
+/*
+ * Cross-leaf kNN (denoise_params.cross_leaf).  The first denoise_set_cross_leaf
+ * (ctx, 1) allocates the variant's per-point tables (neighbour positions for
+ * K = 64, r_K^2, k_eff and a P_1 flag: about 265 bytes a point for max_points);
+ * later forward calls allocate nothing.  A call with cross_leaf = 1 on a context
+ * without them fails with E_STATE.
+ * Errors: E_INVAL (NULL context), E_NOMEM, E_CUDA.
+ */
+int denoise_set_cross_leaf(denoise_ctx *ctx, int enable);
 int denoise_soft_removal(denoise_ctx *ctx, float *removal, void *stream);
 int denoise_backward(denoise_ctx *ctx, const float *grad_removal, double *grad4, void *stream);
 

@@ -33,6 +33,7 @@ EXPORTED = [
     "denoise_get_stats", "denoise_run_debug", "denoise_set_training", "denoise_soft_removal",
     "denoise_backward", "denoise_run_noalloc", "denoise_set_tuning", "denoise_noalloc_scratch_bytes",
     "denoise_set_wait_limit", "denoise_test_hold_lookback", "denoise_eval_metrics", "denoise_run_baseline",
+    "denoise_set_cross_leaf",
 ]
 DENOISE_NOALLOC_MAX_POINTS = 16384
 
@@ -56,6 +57,7 @@ class denoise_params(ctypes.Structure):
         ("temperature", ctypes.c_float),
         ("stage_off", ctypes.c_uint32),
         ("rescore_p2", ctypes.c_uint32),
+        ("cross_leaf", ctypes.c_uint32),
     ]
 
 
@@ -109,7 +111,8 @@ def lib():
     L.denoise_run.argtypes = [_V, _V, ctypes.c_size_t, _P, _V, _V, _V, _V]
     L.denoise_run_batch.argtypes = [_V, _V, ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint32, _P, _V, _V, _V, _V]
     L.denoise_run_debug.argtypes = [_V, _V, ctypes.c_size_t, _P, _V, _V, _V, ctypes.POINTER(denoise_debug), _V]
-    for name in ("denoise_set_sync", "denoise_set_graphs", "denoise_set_profiling", "denoise_set_training"):
+    for name in ("denoise_set_sync", "denoise_set_graphs", "denoise_set_profiling", "denoise_set_training",
+                 "denoise_set_cross_leaf"):
         getattr(L, name).argtypes = [_V, ctypes.c_int]
     L.denoise_get_status.argtypes = [_V, _V]
     L.denoise_get_stats.argtypes = [_V, ctypes.POINTER(denoise_stats)]
@@ -186,6 +189,10 @@ def denoise_set_graphs(ctx, on: int) -> int:
 
 def denoise_set_profiling(ctx, on: int) -> int:
     return lib().denoise_set_profiling(ctx, int(on))
+
+
+def denoise_set_cross_leaf(ctx, on: int) -> int:
+    return lib().denoise_set_cross_leaf(ctx, int(on))
 
 
 def denoise_set_training(ctx, on: int) -> int:

@@ -41,12 +41,13 @@ class Params:
     temperature: float = 0.05
     stage_off: int = 0      # ablations (Table 9): bit 0 no voxel gate, bit 1 no density gate, bit 2 no score
     rescore_p2: int = 0     # 1: the score uses a kNN recomputed within P_2
+    cross_leaf: int = 0     # 1: kNN over the 27 same-level octree cells around the leaf (set_cross_leaf first)
 
     def to_c(self) -> N.denoise_params:
         return N.denoise_params(self.k, self.leaf_capacity, self.max_depth, self.beta, self.min_vox_count,
                                 self.rho_percentile, self.alpha, self.sigma, self.gamma, self.eps_rho,
                                 self.eps_k, self.select_mode, self.lam, self.tau, self.temperature,
-                                self.stage_off, self.rescore_p2)
+                                self.stage_off, self.rescore_p2, self.cross_leaf)
 
 
 @dataclasses.dataclass
@@ -104,6 +105,10 @@ class Denoiser:
     def test_hold_lookback(self, tile: int):
         """Test hook (``denoise_test_hold_lookback``): radix tile ``tile`` never publishes; -1 = off."""
         N.check(N.denoise_test_hold_lookback(self.ctx, int(tile)), "denoise_test_hold_lookback")
+
+    def set_cross_leaf(self, on: bool):
+        """Allocate the cross-leaf kNN tables (``denoise_set_cross_leaf``)."""
+        N.check(N.denoise_set_cross_leaf(self.ctx, on), "denoise_set_cross_leaf")
 
     def set_training(self, on: bool):
         N.check(N.denoise_set_training(self.ctx, on), "denoise_set_training")

@@ -42,6 +42,11 @@ struct denoise_ctx {
   // training cache (allocated by denoise_set_training)
   TrainCache train{};
   bool train_alloc = false;
+  // cross-leaf tables (allocated by denoise_set_cross_leaf), by sorted position
+  uint32_t *x_nbr = nullptr;  // [max_points][64]
+  float *x_r2 = nullptr;
+  uint32_t *x_keff = nullptr;
+  uint8_t *x_flag = nullptr;
   // pinned host memory
   // pinned tile/frame tables: a ring of slots, so that a call with a new frame
   // layout does not wait for the calls still in flight (each slot is rewritten
@@ -124,7 +129,8 @@ int check_params(const denoise_params *p) {
   if (!isfinite(p->eps_rho) || !isfinite(p->eps_k) || !isfinite(p->tau)) return DENOISE_E_INVAL;
   if (p->select_mode > 1) return DENOISE_E_INVAL;
   if (!(p->temperature > 0.0f) || !isfinite(p->temperature)) return DENOISE_E_INVAL;
-  if (p->stage_off > 7u || p->rescore_p2 > 1u) return DENOISE_E_INVAL;
+  if (p->stage_off > 7u || p->rescore_p2 > 1u || p->cross_leaf > 1u) return DENOISE_E_INVAL;
+  if (p->cross_leaf && (p->stage_off || p->rescore_p2)) return DENOISE_E_INVAL;
   return DENOISE_OK;
 }
 
@@ -140,7 +146,8 @@ void free_ctx(denoise_ctx *c) {
   void *dptrs[] = {c->d_xyz, c->d_mask, c->d_score, c->d_stage, c->d_gin, c->d_keys[0], c->d_keys[1],
                    c->d_vals[0], c->d_vals[1], c->d_spts, c->d_frames, c->d_tiles, c->d_hist, c->d_base,
                    c->d_lookback, c->d_leaves, c->d_order, c->d_ctr, c->d_big, c->d_partials, c->d_grad,
-                   c->train.nbr, c->train.nd2, c->train.ell, c->train.r2, c->train.F, c->train.stage};
+                   c->train.nbr, c->train.nd2, c->train.ell, c->train.r2, c->train.F, c->train.stage,
+                   c->x_nbr, c->x_r2, c->x_keff, c->x_flag};
   for (void *p : dptrs)
     if (p) cudaFree(p);
   void *hptrs[] = {c->h_ctr, c->h_grad};
@@ -269,6 +276,34 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
   }
   if (launch_leaf_prep(la, c->num_sms, st, &launches)) return cuda_fail();
   if (use_events) cudaEventRecord(c->ev[4], st);
+  if (p.cross_leaf) {
+    // phase 1 (voxel gates: P_1), the cross-leaf kNN, phase 3 (the per-leaf steps after the kNN)
+    la.xflag = c->x_flag;
+    la.xnbr = c->x_nbr;
+    la.xr2 = c->x_r2;
+    la.xkeff = c->x_keff;
+    la.xphase = 1;
+    if (launch_leaf(la, c->num_sms, st, &launches)) return cuda_fail();
+    XleafArgs xa{};
+    xa.n = n;
+    xa.spts = c->d_spts;
+    xa.keys = c->d_keys[front_passes((int)p.max_depth) & 1];
+    xa.leaves = c->d_leaves;
+    xa.frames = c->d_frames;
+    xa.ctr = c->d_ctr;
+    xa.k = p.k;
+    xa.xflag = c->x_flag;
+    xa.xnbr = c->x_nbr;
+    xa.xr2 = c->x_r2;
+    xa.xkeff = c->x_keff;
+    if (dbg) {
+      xa.dbg = *dbg;
+      xa.use_dbg = 1;
+    }
+    if (launch_xleaf_knn(xa, c->num_sms, st)) return cuda_fail();
+    ++launches;
+    la.xphase = 3;
+  }
   if (launch_leaf(la, c->num_sms, st, &launches)) return cuda_fail();
   if (use_events) cudaEventRecord(c->ev[5], st);
   if (mask_h) cudaMemcpyAsync(mask_h, c->d_mask, n, cudaMemcpyDeviceToHost, st);
@@ -316,6 +351,7 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
   const uint32_t n = (uint32_t)n64;
   if (c->training && !c->train_alloc) return DENOISE_E_STATE;
   if (c->training && p->k > 64) return DENOISE_E_INVAL;
+  if (p->cross_leaf && !c->x_nbr) return DENOISE_E_STATE;
 
   // resolve host / device buffers (device memory of another GPU is rejected)
   const Loc lx = locate(xyz, c->device);
@@ -702,6 +738,31 @@ int denoise_set_training(denoise_ctx *ctx, int enable) {
     ctx->train_alloc = true;
   }
   ctx->training = enable ? 1 : 0;
+  return DENOISE_OK;
+}
+
+int denoise_set_cross_leaf(denoise_ctx *ctx, int enable) {
+  if (!ctx) return DENOISE_E_INVAL;
+  if (enable && !ctx->x_nbr) {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return DENOISE_E_CUDA;
+    const size_t N = ctx->max_points;
+    int e = 0;
+    e |= dalloc(&ctx->x_nbr, N * 64);
+    e |= dalloc(&ctx->x_r2, N);
+    e |= dalloc(&ctx->x_keff, N);
+    e |= dalloc(&ctx->x_flag, N);
+    if (e) {
+      void *ps[] = {ctx->x_nbr, ctx->x_r2, ctx->x_keff, ctx->x_flag};
+      for (void *q : ps)
+        if (q) cudaFree(q);
+      ctx->x_nbr = nullptr;
+      ctx->x_r2 = nullptr;
+      ctx->x_keff = nullptr;
+      ctx->x_flag = nullptr;
+      cudaGetLastError();
+      return DENOISE_E_NOMEM;
+    }
+  }
   return DENOISE_OK;
 }
 

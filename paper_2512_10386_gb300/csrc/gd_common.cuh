@@ -78,10 +78,11 @@ struct Counters {
   uint32_t status;
   uint32_t n_leaves;
   uint32_t leaf_work;                    // persistent leaf-kernel work counter
+  uint32_t leaf_work2;                   // the same for a second leaf-kernel pass (cross-leaf mode)
+  uint32_t xleaf_work;                   // cross-leaf kNN work counter
   uint32_t tile_work[kMaxPasses];        // radix-pass tile counters
   uint32_t cls_count[kLeafClasses];      // leaves per size class
   uint32_t cls_cursor[kLeafClasses];     // fill cursors of the class-ordered leaf list
-  uint32_t pad;
   unsigned long long knn_pairs;
   unsigned long long n_p1;
   unsigned long long n_p2;
@@ -189,7 +190,34 @@ struct LeafArgs {
   uint32_t ctas_per_sm;         // 0 = occupancy limit
   uint32_t threads;             // threads per leaf CTA: 64 or 128 (0 = 128)
   uint32_t spin_limit;          // iterations of the bounded bulk-copy wait (0 = kSpinLimit)
+  // cross-leaf kNN (denoise_params.cross_leaf): phase 1 runs the voxel gate only and
+  // marks P_1; phase 3 runs the per-leaf steps after the kNN on the cross-leaf results
+  uint32_t xphase;              // 0 (the fused method), 1 or 3
+  uint8_t *xflag;               // [n] P_1 membership by sorted position
+  const uint32_t *xnbr;         // [n][k] neighbours (sorted positions), by sorted position
+  const float *xr2;             // [n] floored r_K^2 by sorted position
+  const uint32_t *xkeff;        // [n] k_eff by sorted position (0: no neighbour)
 };
+
+// Cross-leaf kNN (gd_xleaf.cu): for the P_1 points of every leaf, the k_eff
+// nearest (d^2, input index) among the P_1 points of the 27 same-level octree
+// cells around the leaf's cell.
+struct XleafArgs {
+  uint32_t n;
+  const float4 *spts;              // sorted points (x, y, z, input index bits)
+  const unsigned long long *keys;  // sorted Morton keys
+  const Leaf *leaves;
+  const FrameInfo *frames;
+  Counters *ctr;
+  uint32_t k;
+  const uint8_t *xflag;
+  uint32_t *xnbr;
+  float *xr2;
+  uint32_t *xkeff;
+  denoise_debug dbg;
+  int use_dbg;
+};
+int launch_xleaf_knn(const XleafArgs &a, int num_sms, cudaStream_t st);
 
 int leaf_kmax(uint32_t k);
 size_t leaf_smem_bytes(uint32_t lmax, int kmax);

@@ -25,6 +25,8 @@ __global__ void k_init(FrameInfo *frames, uint32_t nframes, Counters *ctr, uint3
     ctr->status = 0;
     ctr->n_leaves = 0;
     ctr->leaf_work = 0;
+    ctr->leaf_work2 = 0;
+    ctr->xleaf_work = 0;
     for (int i = 0; i < kMaxPasses; ++i) ctr->tile_work[i] = 0;
     for (int i = 0; i < kLeafClasses; ++i) ctr->cls_count[i] = ctr->cls_cursor[i] = 0;
     ctr->knn_pairs = 0;
@@ -585,8 +587,11 @@ int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t
   const size_t win = (a.leaf_capacity <= kLeavesSmemCap)
                         ? sizeof(unsigned long long) * (kLeavesPart + 2 * ((size_t)a.leaf_capacity + 1))
                         : 0;
-  launch_pdl(k_leaves, a.ntiles * kLeavesSplit, kFrontThreads, win, st,a.keys[cur], a.tiles, a.frames, a.leaves, a.ctr,
-                                                                a.leaf_capacity, a.max_depth);
+  // a capacity above any frame's size means the same as "the root is a leaf"; clamped
+  // so that the finder's window arithmetic (cap + 1) cannot wrap
+  const uint32_t cap = a.leaf_capacity < (1u << 30) ? a.leaf_capacity : (1u << 30);
+  launch_pdl(k_leaves, a.ntiles * kLeavesSplit, kFrontThreads, win, st, a.keys[cur], a.tiles, a.frames, a.leaves, a.ctr,
+             cap, a.max_depth);
   ++nl;
   if (launches) *launches += nl;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

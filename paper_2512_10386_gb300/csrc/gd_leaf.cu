@@ -176,8 +176,8 @@ uint32_t leaf_big_bpp(int kmax) {
 }
 
 uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit) {
-  uint32_t l = pow2ceil(leaf_capacity < 64 ? 64 : leaf_capacity);
-  if (l > kLeafSmemMax) l = kLeafSmemMax;
+  const uint32_t cap = leaf_capacity < 64 ? 64 : (leaf_capacity > kLeafSmemMax ? kLeafSmemMax : leaf_capacity);
+  uint32_t l = pow2ceil(cap);
   while (l > 64 && leaf_smem_bytes(l, kmax) > smem_limit) l >>= 1;
   return l;
 }

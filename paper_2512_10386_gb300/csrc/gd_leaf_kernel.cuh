@@ -24,9 +24,10 @@ constexpr uint32_t kPad = 32;
 constexpr uint32_t kLeafSmemMax = 2048;
 
 __host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+// smallest power of two >= x (x <= 2^31; larger x gives 2^31)
 __host__ __device__ __forceinline__ uint32_t pow2ceil(uint32_t x) {
   uint32_t p = 1;
-  while (p < x) p <<= 1;
+  while (p < x && p < 0x80000000u) p <<= 1;
   return p;
 }
 
@@ -45,6 +46,7 @@ struct LeafMem {
   float *r2, *wa;            // [cap] per P_1 position: r_K^2, (alpha/2) ell; wa also holds voxel hash slots
   float *F;                  // [cap] score; shares r2's storage (F_i is written after r2_i's last read)
   uint8_t *flag;             // [cap] 0 removed by density gate, 1 scored, 2 kept
+  uint32_t *spos;            // [cap] leaf offset of each P_1 point (cross-leaf mode)
   void *nbr;                 // neighbours: bitmaps (shared-memory path, see bitmap_words) or [KMAX][cap] u32 (global)
   uint32_t nbr_bytes;        // bytes of the region that holds nbr
   uint32_t hcap, scap, cap;
@@ -96,6 +98,7 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
   const size_t soa = (size_t)(cap + kPad) * 4;
   const size_t x = take(soa), y = take(soa), z = take(soa), w = take(soa);
   const size_t r2 = take((size_t)cap * 4), wa = take((size_t)cap * 4), fl = take((size_t)cap);
+  const size_t sp = take((size_t)cap * 4);
   if (m) {
     m->raw = kSmem ? (float4 *)(base + rr) : nullptr;
     m->sbuf = (unsigned long long *)(base + rr);
@@ -108,6 +111,7 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
     m->wa = (float *)(base + wa);
     m->F = m->r2;
     m->flag = (uint8_t *)(base + fl);
+    m->spos = (uint32_t *)(base + sp);
   }
   return o;
 }
@@ -118,6 +122,7 @@ struct LeafShared {
   uint32_t nless, ntied;  // Top-lambda cut: P_2 keys below / equal to the keep_n-th
   uint32_t crank;  // Eq. 14 cut rank c, from the top of the ascending r^2 order
   float lo[3], h, delta, r2ref, Lref;
+  float lshift;  // cross-leaf mode: ell_j = log2(rho_j) - lshift for a neighbour j of any leaf
   double rho_med;
   uint32_t wsum[kLeafWarps];
   uint32_t red[kLeafWarps][6];
@@ -488,7 +493,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       }
       const uint32_t c = a1_on ? M.hcnt[vslot[i]] : 0u;
       in1 = !a1_on || c >= P.min_vox_count;
-      if ((kRec && A.use_dbg)) {
+      if (A.xphase == 1) A.xflag[lf.start + i] = in1 ? 1 : 0;
+      if ((kRec && A.use_dbg) && A.xphase != 3) {
         if (A.dbg.vox_count) A.dbg.vox_count[g] = c;
         if (A.dbg.leaf_start) A.dbg.leaf_start[g] = lf.start - fbeg;
         if (A.dbg.leaf_count) A.dbg.leaf_count[g] = nt;
@@ -496,7 +502,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         if (A.dbg.leaf_rho_med) A.dbg.leaf_rho_med[g] = 0.0;
         if (A.dbg.r2) A.dbg.r2[g] = 0.0f;
       }
-      if (!in1) write_point<kRec>(A, g, 0, 0.0f, 1);
+      if (!in1 && A.xphase != 1) write_point<kRec>(A, g, 0, 0.0f, 1);
     }
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, in1);
     if (lane == 0) S.wsum[w] = __popc(bal);
@@ -509,6 +515,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       Y[pos] = p.y;
       Z[pos] = p.z;
       W[pos] = g;
+      M.spos[pos] = i;
     }
     __syncthreads();
     if (tid == 0) {
@@ -518,6 +525,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     }
     __syncthreads();
   }
+  if (A.xphase == 1) return;  // cross-leaf mode: P_1 is marked, the kNN runs across leaves next
   uint32_t n1 = S.run;  // |P_1|; |P_2| once P_2 is compacted for its own kNN
   for (uint32_t u = tid; u < kPad; u += NT) {  // the NaN padding after P_1
     X[n1 + u] = __int_as_float(0x7FFFFFFF);
@@ -542,6 +550,16 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     return;
   }
   uint32_t keff = (P.k < n1 - 1) ? P.k : n1 - 1;
+  const bool xl = A.xphase == 3;  // cross-leaf mode: the kNN ran across leaves
+  if (xl) {
+    // k_eff is the leaf's (its candidates are shared by its points); 0: no neighbour at all
+    keff = A.xkeff[lf.start + M.spos[0]];
+    if (keff == 0) {
+      for (uint32_t i = tid; i < n1; i += NT) write_point<kRec>(A, W[i], 0, 0.0f, 2);
+      return;
+    }
+    for (uint32_t i = tid; i < n1; i += NT) M.r2[i] = A.xr2[lf.start + M.spos[i]];
+  }
   // the neighbour bitmap (shared-memory path): region A if it fits, else the spill area
   auto bitmap_at = [&](uint32_t n) {
     return (bitmap_words(n) * 4u <= M.nbr_bytes) ? reinterpret_cast<uint32_t *>(M.nbr)
@@ -549,7 +567,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   };
   uint32_t *tbl = bitmap_at(n1);
   if (tid == 0) {
-    atomicAdd(&A.ctr->knn_pairs, (unsigned long long)n1 * (unsigned long long)(n1 - 1));
+    if (!xl) atomicAdd(&A.ctr->knn_pairs, (unsigned long long)n1 * (unsigned long long)(n1 - 1));
     atomicAdd(&A.ctr->n_p1, (unsigned long long)n1);
   }
   if (tid == NT - 1) {  // Eq. 14 rank (FP64, one thread), taken off the later critical path
@@ -575,7 +593,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   // parks B's few members, which are sorted to finish the set.  A boundary
   // bucket with more members than the buffer is counted again at 32 times the
   // resolution first.  Ties in d^2 across the cut are broken by input index.
-  if (keff > 0) {  // (a single point of P_2 has no neighbour to score with: F = 0)
+  if (keff > 0 && !xl) {  // (a single point of P_2 has no neighbour to score with: F = 0)
     constexpr int PL = kPacked ? 11 : 21;  // count planes: counts < 2^PL (n1 - 1 candidates)
     if (!kPacked && n1 >= (1u << PL)) {     // beyond the spill path's counters: refuse, do not guess
       if (tid == 0) atomicOr(&A.ctr->status, kStInternal);
@@ -926,6 +944,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     const float rb = (m & 1u) ? ra : __uint_as_float(vbuf[m / 2]);
     S.r2ref = ra;
     S.Lref = leaf_lref(ra, rb, m, keff, P.eps_rho);
+    S.lshift = __fsub_rn(__fsub_rn(__fsub_rn(log2f((float)keff), 2.0665336287511624f), __fmul_rn(1.5f, log2f(ra))),
+                         S.Lref);
     S.keep_n = (uint32_t)ceil((double)P.lambda * (double)m);
     if (S.keep_n > m) S.keep_n = m;
     atomicAdd(&A.ctr->n_p2, (unsigned long long)m);
@@ -992,6 +1012,28 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         const float D = g2 ? d2 : pow_half_gamma(d2, hg);                    // (d^2)^(gamma/2)
         return __fmul_rn(wt, rcp_hw(__fadd_rn(D, ek)));                    // kernel of Eq. 20
       };
+      if (xl) {
+        // cross-leaf neighbours: coordinates and densities from the global results,
+        // ell_j = log2(rho_j) - lshift with rho_j from the neighbour's own k_eff and r_K
+        const uint32_t *nl = A.xnbr + (size_t)(lf.start + M.spos[i]) * P.k;
+        const float half_alpha = __fmul_rn(0.5f, P.alpha), lsh = S.lshift;
+#pragma unroll 1
+        for (uint32_t t = 0; t < keff; ++t) {
+          const uint32_t j = nl[t];
+          const float4 pj = A.spts[j];
+          const float d2 = sqdist(xi, yi, zi, pj.x, pj.y, pj.z);
+          const float lj = __fsub_rn(__fsub_rn(log2f((float)A.xkeff[j]), 2.0665336287511624f),
+                                     __fmul_rn(1.5f, log2f(A.xr2[j])));
+          const float waj = __fmul_rn(half_alpha, __fsub_rn(lj, lsh));
+          const float wt = ex2_hw(__fmaf_rn(-d2, ci, __fadd_rn(ai, waj)));
+          const float D = g2 ? d2 : pow_half_gamma(d2, hg);
+          const float e = __fmul_rn(wt, rcp_hw(__fadd_rn(D, ek)));
+          if (t & 1u) F1 = __fadd_rn(F1, e);
+          else F0 = __fadd_rn(F0, e);
+        }
+        M.F[i] = __fadd_rn(F0, F1);
+        continue;
+      }
       // two ranks per step (two independent chains); with k_eff odd the last step's
       // second term is computed on the first neighbour again and dropped
 #pragma unroll 1
@@ -1113,7 +1155,10 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : GD_LEAF_MIN_C
   const uint32_t n_leaves = A.ctr->n_leaves;
   uint32_t phase = 0;
   for (;;) {
-    if (tid == 0) S.leaf = (ld_volatile(&A.ctr->status) & kStFatal) ? 0xFFFFFFFFu : atomicAdd(&A.ctr->leaf_work, 1u);
+    if (tid == 0)
+      S.leaf = (ld_volatile(&A.ctr->status) & kStFatal)
+                   ? 0xFFFFFFFFu
+                   : atomicAdd(A.xphase == 3 ? &A.ctr->leaf_work2 : &A.ctr->leaf_work, 1u);
     __syncthreads();
     const uint32_t wi = S.leaf;  // block-uniform: one thread decided
     if (wi >= n_leaves) break;

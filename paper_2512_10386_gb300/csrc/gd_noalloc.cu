@@ -72,7 +72,7 @@ int params_ok(const denoise_params *p) {
   if (!isfinite(p->alpha) || !(p->eps_rho >= 0.0f) || !(p->eps_k >= 0.0f)) return 0;
   if (!isfinite(p->eps_rho) || !isfinite(p->eps_k) || !isfinite(p->tau)) return 0;
   if (p->select_mode > 1 || !(p->temperature > 0.0f) || !isfinite(p->temperature)) return 0;
-  if (p->stage_off > 7u || p->rescore_p2 > 1u) return 0;
+  if (p->stage_off > 7u || p->rescore_p2 > 1u || p->cross_leaf) return 0;  // (no cross-leaf tables here)
   return 1;
 }
 

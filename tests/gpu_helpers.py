@@ -11,7 +11,7 @@ def oracle_params(P):
                          min_vox_count=P.min_vox_count, rho_percentile=P.rho_percentile, alpha=P.alpha,
                          sigma=P.sigma, gamma=P.gamma, eps_rho=P.eps_rho, eps_k=P.eps_k,
                          select_mode=P.select_mode, lam=P.lam, tau=P.tau, temperature=P.temperature,
-                         stage_off=P.stage_off, rescore_p2=P.rescore_p2)
+                         stage_off=P.stage_off, rescore_p2=P.rescore_p2, cross_leaf=P.cross_leaf)
 
 
 def to_np(d):

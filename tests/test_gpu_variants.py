@@ -68,3 +68,44 @@ def test_without_octree_single_leaf(env):
     stats, g, r = _run(env, xyz, k=16, leaf_capacity=0xFFFFFFFF)
     assert r["n_leaves"] == 1 and int(g["leaf_count"][0]) == len(xyz)
     print("without octree:", stats)
+
+
+# ---------------------------------------------------------------------------
+# cross-leaf kNN (candidates from the 27 same-level cells around a leaf)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [8, 16, 32])
+def test_cross_leaf_knn(env, k):
+    import synth
+    orc, d = env
+    d.set_cross_leaf(True)
+    xyz, _ = synth.object_cloud(seed=95 + k, n_surface=8000)
+    stats, g, r = _run(env, xyz, k=k, leaf_capacity=256, cross_leaf=1)
+    print(f"cross-leaf k={k}:", stats)
+
+
+def test_cross_leaf_threshold_mode_and_dense_blob(env):
+    orc, d = env
+    d.set_cross_leaf(True)
+    rng = np.random.default_rng(96)
+    xyz = np.concatenate([rng.normal(size=(6000, 3)) * 0.2, rng.uniform(-2, 2, size=(600, 3))]).astype(np.float32)
+    _run(env, xyz, k=12, leaf_capacity=128, cross_leaf=1, select_mode=1, tau=5.0, rho_percentile=5.0)
+
+
+def test_cross_leaf_requires_its_tables_and_excludes_other_variants():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2512_10386_gb300 import Denoiser, Params
+    from paper_2512_10386_gb300 import _native as N
+    d = Denoiser(max_points=1000)
+    try:
+        x = torch.rand((1000, 3), device="cuda")
+        with pytest.raises(N.DenoiseError) as e:
+            d.run(x, Params(k=8, cross_leaf=1))
+        assert e.value.status == N.DENOISE_E_STATE
+        d.set_cross_leaf(True)
+        d.run(x, Params(k=8, cross_leaf=1))
+        with pytest.raises(N.DenoiseError) as e:
+            d.run(x, Params(k=8, cross_leaf=1, stage_off=1))
+        assert e.value.status == N.DENOISE_E_INVAL
+    finally:
+        d.close()
