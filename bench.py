@@ -87,6 +87,22 @@ def max_over_ranks(value: float, device: str) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(value: float, device: str) -> float:
+    """The units all ranks processed (each rank may hold a different cloud)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(units: float, total_ms: float, device: str) -> float:
+    """Whole-job throughput: the units of all ranks over the slowest rank's time."""
+    return sum_over_ranks(units, device) / (max_over_ranks(total_ms, device) / 1000.0)
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -151,7 +167,7 @@ class ClockSampler:
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("gd_leaf.cu", "gd_leaf_kernel.cuh", "gd_common.cuh"):
+    for f in ("gd_leaf.cu", "gd_leaf_kernel.cuh", "gd_common.cuh", "gd_knn_select.cuh", "gd_f32x2.cuh"):
         with open(os.path.join(ROOT, "paper_2512_10386_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -340,13 +356,24 @@ def run_ours(args):
             flush.fill_(float(s))
         d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
         leaf_ms.append(d.stats()["stage_ms"][4])
-    d.set_profiling(False)
     stats = d.stats()
+    # the same cloud with the score stage switched off (A3: P_2 kept, no score, no
+    # selection): the difference is the time of the score and selection phases
+    P_noscore = Params(k=32, leaf_capacity=512, stage_off=4)
+    out_ns = d.run(xyz, P_noscore, stream=stream)
+    leaf_ms_noscore = []
+    for s in range(min(args.steps, 10)):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(s))
+        d.run(xyz, P_noscore, mask=out_ns.mask, score=out_ns.score, stage=out_ns.stage, stream=stream)
+        leaf_ms_noscore.append(d.stats()["stage_ms"][4])
+    d.set_profiling(False)
+    del out_ns
     launches = stats["launches"] * args.steps
     total_ms = max_over_ranks(sum(step_ms), "cuda")
+    value = job_throughput(n * args.steps, sum(step_ms), "cuda")
     if dist:
         dist.barrier()
-    value = n * world * args.steps / (total_ms / 1000.0)
 
     # ---- roofline of the fused leaf kernel (kNN + score)
     peaks, peak_kind = _peaks()
@@ -362,14 +389,21 @@ def run_ours(args):
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:g} MHz "
                               f"(max SM clock, {peak_kind} peaks file)",
                 "leaf_kernel_ms": leaf_avg_ms, "share_of_step": leaf_avg_ms / (total_ms / args.steps)}
-    # the score's SFU work (ex2 + rcp per neighbour term) over the whole leaf kernel's time:
-    # a lower bound of the score phase's own SFU fraction (the kernel also runs the other phases)
+    # the score's SFU work (ex2 + rcp per neighbour term) over the score phase's time, taken as
+    # the leaf kernel's time minus its time with the score stage off (that difference also holds
+    # the Top-lambda selection, so the fraction is a lower bound of the score phase's own); the
+    # fraction over the whole kernel's time is reported beside it
     xu_peak = props.multi_processor_count * XU_PER_SM_CLK * sm_mhz * 1e6 / 1e12
-    xu_achieved = stats["score_terms"] * XU_OPS_PER_TERM / (leaf_avg_ms / 1000.0) / 1e12
+    xu_ops = stats["score_terms"] * XU_OPS_PER_TERM
+    noscore_ms = sum(leaf_ms_noscore) / len(leaf_ms_noscore)
+    score_phase_ms = max(leaf_avg_ms - noscore_ms, 1e-6)
+    xu_achieved = xu_ops / (score_phase_ms / 1000.0) / 1e12
     roofline_score = {"bound": "xu", "achieved": xu_achieved, "peak": xu_peak, "unit": "Tops/s",
                       "frac": xu_achieved / xu_peak,
                       "work": f"{stats['score_terms']} neighbour terms x {XU_OPS_PER_TERM:g} SFU ops (ex2, rcp)",
-                      "time_basis": "the whole fused leaf kernel (the score is one of its phases)",
+                      "time_basis": "score + selection phases: leaf kernel with the score stage minus without it",
+                      "score_phase_ms": score_phase_ms, "leaf_kernel_ms_score_off": noscore_ms,
+                      "frac_over_whole_kernel": xu_ops / (leaf_avg_ms / 1000.0) / 1e12 / xu_peak,
                       "peak_basis": f"{props.multi_processor_count} SMs x {XU_PER_SM_CLK:g} SFU ops/clk x {sm_mhz:g} MHz"}
 
     # ---- the timed cloud's result against the FP64 oracle (outside every timed region)

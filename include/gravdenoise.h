@@ -96,8 +96,11 @@ typedef struct denoise_ctx denoise_ctx;
  * All device scratch of the forward path (sort buffers, octree leaf table,
  * per-leaf spill space) is allocated here, sized for max_points; the forward
  * calls (denoise_run, denoise_run_batch, denoise_run_debug) allocate no device
- * memory.  The one later allocation is the training cache, made by the first
- * denoise_set_training(ctx, 1) (about 520 bytes a point).  The largest buffer
+ * memory.  Two optional features allocate later, on request: the training
+ * cache, made by the first denoise_set_training(ctx, 1) (about 520 bytes a
+ * point), and the cross-leaf kNN tables, made by the first
+ * denoise_set_cross_leaf(ctx, 1) (about 265 bytes a point); the metric and
+ * baseline calls use the context's scratch and allocate nothing.  The largest buffer
  * is allocated first, so a context too large for the GPU fails with E_NOMEM
  * before it holds any memory.  *out receives the context (NULL on failure).
  * Errors: E_INVAL (out NULL, max_points or max_frames 0), E_NOMEM, E_CUDA.
@@ -315,15 +318,17 @@ int denoise_backward(denoise_ctx *ctx, const float *grad_removal, double *grad4,
  *        pointers of another GPU are rejected).
  *  mask, score, stage: as denoise_run, DEVICE pointers or NULL.
  *  Works on the calling thread's current CUDA device.  The first call on a
- *  device looks up the scratch array's device address (cudaGetSymbolAddress);
- *  make that first call before any stream capture.  Each call synchronises
- *  `stream` and returns the device-side status.
+ *  device looks up the scratch array's device address (cudaGetSymbolAddress).
+ *  Each call synchronises `stream` and returns the device-side status, so no
+ *  call can be recorded into a CUDA graph: a call on a stream that is being
+ *  captured returns E_INVAL and enqueues nothing.
  *  All calls share the one scratch array, and it keeps the last call's
  *  contents (the call clears what must start at zero): calls that overlap on
  *  the GPU -- from two host threads, or on two streams -- race and must not
  *  be made.
- * Errors: E_INVAL (NULL or host xyz/outputs, bad parameters), E_CAPACITY
- * (n > DENOISE_NOALLOC_MAX_POINTS), E_NONFINITE, E_TIMEOUT, E_CUDA.
+ * Errors: E_INVAL (NULL, host or other-GPU xyz/outputs, bad parameters, a
+ * capturing stream), E_CAPACITY (n > DENOISE_NOALLOC_MAX_POINTS), E_NONFINITE,
+ * E_TIMEOUT, E_CUDA.
  */
 #define DENOISE_NOALLOC_MAX_POINTS 16384u
 int denoise_run_noalloc(const float *xyz, size_t n, const denoise_params *p, uint8_t *mask, float *score,

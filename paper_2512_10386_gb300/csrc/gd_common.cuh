@@ -229,6 +229,7 @@ int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launc
 int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches);
 // the recording instantiation (debug / training outputs), in its own translation unit
 int launch_leaf_rec(const LeafArgs &a, int num_sms, cudaStream_t st);
+int launch_leaf_xl(const LeafArgs &a, int num_sms, cudaStream_t st);
 
 // Evaluation metrics (Eq. 29-30) and the baseline of Sec. 2.2 (gd_eval.cu).
 struct EvalArgs {

@@ -192,7 +192,8 @@ int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launc
 
 int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches) {
   if (launches) ++*launches;
-  return (a.use_dbg || a.use_train) ? launch_leaf_rec(a, num_sms, st) : launch_kmax<false>(a, num_sms, st);
+  if (a.xphase != 0) return launch_leaf_xl(a, num_sms, st);  // the cross-leaf phases: their own instantiation
+  return (a.use_dbg || a.use_train) ? launch_leaf_rec(a, num_sms, st) : launch_kmax<false, false>(a, num_sms, st);
 }
 
 }  // namespace gd

@@ -47,6 +47,8 @@ struct LeafMem {
   float *F;                  // [cap] score; shares r2's storage (F_i is written after r2_i's last read)
   uint8_t *flag;             // [cap] 0 removed by density gate, 1 scored, 2 kept
   uint32_t *spos;            // [cap] leaf offset of each P_1 point (cross-leaf mode)
+  uint32_t *cmask;           // [cap] the chunks of a query's bitmap row that hold neighbours (shares spos:
+                             // the cross-leaf mode, which reads spos later, runs no kNN in this kernel)
   void *nbr;                 // neighbours: bitmaps (shared-memory path, see bitmap_words) or [KMAX][cap] u32 (global)
   uint32_t nbr_bytes;        // bytes of the region that holds nbr
   uint32_t hcap, scap, cap;
@@ -112,6 +114,7 @@ __host__ __device__ __forceinline__ size_t carve(unsigned char *base, uint32_t c
     m->F = m->r2;
     m->flag = (uint8_t *)(base + fl);
     m->spos = (uint32_t *)(base + sp);
+    m->cmask = m->spos;
   }
   return o;
 }
@@ -121,6 +124,7 @@ struct LeafShared {
   uint32_t n1, keff, m, keep_n, run;
   uint32_t nless, ntied;  // Top-lambda cut: P_2 keys below / equal to the keep_n-th
   uint32_t crank;  // Eq. 14 cut rank c, from the top of the ascending r^2 order
+  uint32_t qblk;   // next 32-query block of the kNN
   float lo[3], h, delta, r2ref, Lref;
   float lshift;  // cross-leaf mode: ell_j = log2(rho_j) - lshift for a neighbour j of any leaf
   double rho_med;
@@ -403,15 +407,51 @@ __device__ __forceinline__ bool rec_index_ok(const LeafArgs &A, uint32_t g) {
   return false;
 }
 
+// L2 eviction policies.  The leaf's packed points are read once (evict first);
+// the outputs are written by input index, so a 32-byte sector of them is
+// completed by several leaves at different times: kept in L2 (evict last) a
+// sector is merged there, evicted half written it costs a DRAM read-modify-write.
+#ifndef GD_SCORE_CHAINS
+#define GD_SCORE_CHAINS 2
+#endif
+#ifndef GD_LEAF_L2HINT
+#define GD_LEAF_L2HINT 1
+#endif
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void st_keep_u8(uint8_t *p, uint32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u8 [%0], %1, %2;" ::"l"(__cvta_generic_to_global(p)), "r"(v), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st_keep_f32(float *p, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(__cvta_generic_to_global(p)), "f"(v), "l"(pol)
+               : "memory");
+}
+
 template <bool kRec>
 __device__ __forceinline__ void write_point(const LeafArgs &A, uint32_t g, uint8_t mk, float sc, uint8_t st) {
   if (g >= A.n) {  // cannot happen with a consistent sort; never write out of bounds
     atomicOr(&A.ctr->status, kStInternal);
     return;
   }
+#if GD_LEAF_L2HINT
+  const uint64_t pol = l2_evict_last();
+  if (A.mask) st_keep_u8(A.mask + g, mk, pol);
+  if (A.score) st_keep_f32(A.score + g, sc, pol);
+  if (A.stage) st_keep_u8(A.stage + g, st, pol);
+#else
   if (A.mask) A.mask[g] = mk;
   if (A.score) A.score[g] = sc;
   if (A.stage) A.stage[g] = st;
+#endif
   if (kRec && A.use_train) {
     A.train.stage[g] = st;
     A.train.F[g] = sc;
@@ -421,7 +461,7 @@ __device__ __forceinline__ void write_point(const LeafArgs &A, uint32_t g, uint8
 // ---------------------------------------------------------------------------
 // one leaf
 // ---------------------------------------------------------------------------
-template <int KMAX, typename IdxT, bool kRec>
+template <int KMAX, typename IdxT, bool kRec, bool kXl>
 __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__restrict__ pts, const LeafMem &M,
                              LeafShared &S) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -493,8 +533,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       }
       const uint32_t c = a1_on ? M.hcnt[vslot[i]] : 0u;
       in1 = !a1_on || c >= P.min_vox_count;
-      if (A.xphase == 1) A.xflag[lf.start + i] = in1 ? 1 : 0;
-      if ((kRec && A.use_dbg) && A.xphase != 3) {
+      if (kXl && A.xphase == 1) A.xflag[lf.start + i] = in1 ? 1 : 0;
+      if ((kRec && A.use_dbg) && !(kXl && A.xphase == 3)) {
         if (A.dbg.vox_count) A.dbg.vox_count[g] = c;
         if (A.dbg.leaf_start) A.dbg.leaf_start[g] = lf.start - fbeg;
         if (A.dbg.leaf_count) A.dbg.leaf_count[g] = nt;
@@ -502,7 +542,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         if (A.dbg.leaf_rho_med) A.dbg.leaf_rho_med[g] = 0.0;
         if (A.dbg.r2) A.dbg.r2[g] = 0.0f;
       }
-      if (!in1 && A.xphase != 1) write_point<kRec>(A, g, 0, 0.0f, 1);
+      if (!in1 && !(kXl && A.xphase == 1)) write_point<kRec>(A, g, 0, 0.0f, 1);
     }
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, in1);
     if (lane == 0) S.wsum[w] = __popc(bal);
@@ -525,7 +565,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     }
     __syncthreads();
   }
-  if (A.xphase == 1) return;  // cross-leaf mode: P_1 is marked, the kNN runs across leaves next
+  if (kXl && A.xphase == 1) return;  // cross-leaf mode: P_1 is marked, the kNN runs across leaves next
   uint32_t n1 = S.run;  // |P_1|; |P_2| once P_2 is compacted for its own kNN
   for (uint32_t u = tid; u < kPad; u += NT) {  // the NaN padding after P_1
     X[n1 + u] = __int_as_float(0x7FFFFFFF);
@@ -550,7 +590,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     return;
   }
   uint32_t keff = (P.k < n1 - 1) ? P.k : n1 - 1;
-  const bool xl = A.xphase == 3;  // cross-leaf mode: the kNN ran across leaves
+  const bool xl = kXl && A.xphase == 3;  // cross-leaf mode: the kNN ran across leaves
   if (xl) {
     // k_eff is the leaf's (its candidates are shared by its points); 0: no neighbour at all
     keff = A.xkeff[lf.start + M.spos[0]];
@@ -574,6 +614,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     const double pos = __dadd_rn(__ddiv_rn(__dmul_rn((double)n1, (double)P.rho_percentile), 100.0), 0.5);
     const double cc = ceil(pos);
     S.crank = !a2_on ? 1u : (cc < 1.0) ? 1u : (cc > (double)n1) ? n1 : (uint32_t)cc;  // rank 1: nothing removed
+    S.qblk = NW;
   }
   uint32_t sn = pow2ceil(n1);
   __syncthreads();  // P_1 and its padding complete
@@ -606,10 +647,15 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     const uint32_t pmask = (1u << pbits) - 1u;
     const uint32_t n16 = (n1 + 15u) >> 4;
     const bool dbg_n = (kRec && A.use_dbg) && A.dbg.nbr, dbg_d = (kRec && A.use_dbg) && A.dbg.nbr_d2;
-    for (uint32_t qb = 0; qb < n1; qb += NT) {
-      const uint32_t q = qb + tid;
+    const bool use_cm = kPacked && n1 <= 1024u;  // bitmap rows of at most 32 words: chunk masks
+    // the queries in blocks of 32, one block per warp at a time, taken first come
+    // first served: a warp whose block needed a refinement pass does not hold the
+    // next blocks back (warp w starts with block w, then takes S.qblk's next)
+    const uint32_t nblk = (n1 + 31u) >> 5;
+#pragma unroll 1
+    for (uint32_t blk = w; blk < nblk;) {
+      const uint32_t q = blk * 32u + lane;
       const bool act = q < n1;
-      if (!__any_sync(0xFFFFFFFFu, act)) continue;  // whole warp idle (warp-uniform)
       const uint32_t qq = act ? q : n1 - 1;          // idle lanes shadow a real query, results discarded
       const float xq = X[qq], yq = Y[qq], zq = Z[qq];
       const uint32_t gq = W[qq];
@@ -687,6 +733,18 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       // Ranks come in order t = 0, 1, ...: the packed table is filled through a
       // bit buffer, one word store per 32 bits.
       uint32_t *const nbw = tbl + qq;  // this query's bitmap column: word c at nbw[c * n1]
+      // with at most 32 chunks, only the words that hold neighbours are stored, and
+      // cm marks them (the score reads those alone); otherwise every word is stored
+      uint32_t cm = 0;
+      auto set_bit = [&](uint32_t ju) {
+        const uint32_t cw = ju >> 5, bit = 1u << (ju & 31u);
+        if (!use_cm || ((cm >> cw) & 1u)) {
+          nbw[(size_t)cw * n1] |= bit;
+        } else {
+          nbw[(size_t)cw * n1] = bit;
+          cm |= 1u << cw;
+        }
+      };
       // Record neighbour t (position npos, input index g, distance d2) where the
       // table keeps positions (global path) and in the debug / training outputs.
       auto emit = [&](uint32_t t, uint32_t npos, uint32_t g, float d2) {
@@ -740,7 +798,9 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         if (!act || ties_only || np > kSelBuf) pm = 0;
         uint32_t t = a - __popc(em), slot = np - __popc(pm);
         if constexpr (kPacked) {
-          if (act) nbw[(size_t)(c0 >> 5) * n1] = em;  // the chunk's neighbours below the boundary bucket, one store
+          // the chunk's neighbours below the boundary bucket, one store
+          if (act && (em || !use_cm)) nbw[(size_t)(c0 >> 5) * n1] = em;
+          cm |= (em ? 1u : 0u) << ((c0 >> 5) & 31u);
         }
         if constexpr (!kPacked || kRec) {
           while (em) {
@@ -798,7 +858,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           const uint32_t i = (uint32_t)(__ffs(take) - 1);
           take &= take - 1u;
           const uint32_t key = pend[i * kLeafThreads + tid], ju = key & pmask;
-          if constexpr (kPacked) nbw[(size_t)(ju >> 5) * n1] |= 1u << (ju & 31u);
+          if constexpr (kPacked) set_bit(ju);
           emit(a++, ju, W[ju], __int_as_float(kbase + (int32_t)(key >> pbits)));
         }
       }
@@ -820,7 +880,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           }
         }
         if (r < rounds) {
-          if constexpr (kPacked) nbw[(size_t)(bp >> 5) * n1] |= 1u << (bp & 31u);
+          if constexpr (kPacked) set_bit(bp);
           emit(a++, bp, bg, hi_f);
           last = bg;
         }
@@ -845,6 +905,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         if (a != keff) atomicOr(&A.ctr->status, kStInternal);
         const float rt = (theta < delta2) ? delta2 : theta;
         M.r2[qq] = rt;
+        if (kPacked && use_cm) M.cmask[qq] = cm;
         if (kRec && (A.use_dbg || A.use_train) && rec_index_ok(A, gq)) {
           for (uint32_t t = keff; t < P.k; ++t) {
             if (dbg_n) A.dbg.nbr[(size_t)gq * P.k + t] = 0xFFFFFFFFu;
@@ -858,6 +919,9 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           if (A.use_train) A.train.r2[gq] = rt;
         }
       }
+      uint32_t nb = 0;
+      if (lane == 0) nb = atomicAdd(&S.qblk, 1u);
+      blk = __shfl_sync(0xFFFFFFFFu, nb, 0);
     }
   }
   __syncthreads();
@@ -929,6 +993,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   keff = n1 <= 1 ? 0u : (P.k < n1 - 1) ? P.k : n1 - 1;
   tbl = bitmap_at(n1);
   sn = pow2ceil(n1);
+  if (tid == 0) S.qblk = NW;
   if (tid == 0 && keff) atomicAdd(&A.ctr->knn_pairs, (unsigned long long)n1 * (unsigned long long)(n1 - 1));
   __syncthreads();
   }  // kpass
@@ -993,12 +1058,42 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
       // neighbours in position order: from the bitmap row (shared memory) or the
       // position-ordered list (global path)
       const uint32_t *row = tbl + i;  // word c at row[c * n1]
-      uint32_t rc = 0, rm = kPacked ? row[0] : 0u;
+      // with chunk masks (at most 32 words) only the words that hold neighbours are
+      // read, the next one loaded while the current one is consumed (the row may be
+      // in the spill area); otherwise the row is read word by word
       const uint32_t rwords = (n1 + 31u) >> 5;
+      const bool cmk_on = !xl && kPacked && n1 <= 1024u;
+      // the mask is written by the kNN of this leaf (k_eff > 0); only chunks of the row are taken
+      uint32_t cmk = (cmk_on && keff > 0) ? M.cmask[i] & ((rwords >= 32u) ? 0xFFFFFFFFu : ((1u << rwords) - 1u)) : 0u;
+      auto pop_chunk = [&]() -> uint32_t {  // next chunk of the mask (32 if none is left)
+        const uint32_t c = cmk ? (uint32_t)(__ffs(cmk) - 1) : 32u;
+        cmk &= cmk - 1u;
+        return c;
+      };
+      uint32_t rc = 0, rm = 0, pc = 32, pm = 0;
+      if (kPacked && !xl && keff > 0) {
+        if (cmk_on) {
+          rc = pop_chunk();
+          rm = rc < 32u ? row[(size_t)rc * n1] : 0u;
+          pc = pop_chunk();
+          pm = pc < 32u ? row[(size_t)pc * n1] : 0u;
+        } else {
+          rm = row[0];
+        }
+      }
       auto next_j = [&](uint32_t t, bool valid) -> uint32_t {  // called for t = 0, 1, ... in order
         if constexpr (kPacked) {
           if (!valid) return 0u;
-          while (rm == 0u && rc + 1 < rwords) rm = row[(size_t)(++rc) * n1];
+          if (cmk_on) {
+            while (rm == 0u && pc < 32u) {  // take the prefetched word, load the one after it
+              rm = pm;
+              rc = pc;
+              pc = pop_chunk();
+              pm = pc < 32u ? row[(size_t)pc * n1] : 0u;
+            }
+          } else {
+            while (rm == 0u && rc + 1 < rwords) rm = row[(size_t)(++rc) * n1];
+          }
           const uint32_t j = (rc << 5) + (uint32_t)(__ffs(rm) - 1);  // rm == 0 only if the row is inconsistent
           rm &= rm - 1u;
           return j < n1 ? j : 0u;
@@ -1034,6 +1129,26 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         M.F[i] = __fadd_rn(F0, F1);
         continue;
       }
+#if GD_SCORE_CHAINS == 4
+      // four ranks per step (four independent chains, rank t into sum t mod 4);
+      // missing ranks of the last step are computed on the first neighbour again and dropped
+      float F2 = 0.0f, F3 = 0.0f;
+#pragma unroll 1
+      for (uint32_t t = 0; t < keff; t += 4) {
+        const bool v1 = t + 1 < keff, v2 = t + 2 < keff, v3 = t + 3 < keff;
+        const uint32_t ja = next_j(t, true);
+        uint32_t jb = next_j(t + 1, v1), jc = next_j(t + 2, v2), jd = next_j(t + 3, v3);
+        jb = v1 ? jb : ja;
+        jc = v2 ? jc : ja;
+        jd = v3 ? jd : ja;
+        const float e0 = term(ja), e1 = term(jb), e2 = term(jc), e3 = term(jd);
+        F0 = __fadd_rn(F0, e0);
+        if (v1) F1 = __fadd_rn(F1, e1);
+        if (v2) F2 = __fadd_rn(F2, e2);
+        if (v3) F3 = __fadd_rn(F3, e3);
+      }
+      M.F[i] = __fadd_rn(__fadd_rn(F0, F1), __fadd_rn(F2, F3));
+#else
       // two ranks per step (two independent chains); with k_eff odd the last step's
       // second term is computed on the first neighbour again and dropped
 #pragma unroll 1
@@ -1047,6 +1162,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         if (two) F1 = __fadd_rn(F1, e1);
       }
       M.F[i] = __fadd_rn(F0, F1);
+#endif
     }
   }
   __syncthreads();
@@ -1135,7 +1251,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, uint32_t
 #ifndef GD_LEAF_MIN_CTAS
 #define GD_LEAF_MIN_CTAS 6
 #endif
-template <int KMAX, bool kRec>
+template <int KMAX, bool kRec, bool kXl>
 __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : GD_LEAF_MIN_CTAS) k_leaf(const LeafArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long s_mbar;
@@ -1158,7 +1274,7 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : GD_LEAF_MIN_C
     if (tid == 0)
       S.leaf = (ld_volatile(&A.ctr->status) & kStFatal)
                    ? 0xFFFFFFFFu
-                   : atomicAdd(A.xphase == 3 ? &A.ctr->leaf_work2 : &A.ctr->leaf_work, 1u);
+                   : atomicAdd((kXl && A.xphase == 3) ? &A.ctr->leaf_work2 : &A.ctr->leaf_work, 1u);
     __syncthreads();
     const uint32_t wi = S.leaf;  // block-uniform: one thread decided
     if (wi >= n_leaves) break;
@@ -1169,10 +1285,18 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : GD_LEAF_MIN_C
         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s_pts);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+#if GD_LEAF_L2HINT
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+            "%4;" ::"r"(dst),
+            "l"(__cvta_generic_to_global(A.spts + lf.start)), "r"(bytes), "r"(bar), "l"(l2_evict_first())
+            : "memory");
+#else
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
             "l"(__cvta_generic_to_global(A.spts + lf.start)), "r"(bytes), "r"(bar)
             : "memory");
+#endif
       }
       const bool ok = mbar_wait(bar, phase, A.spin_limit);
       if (__syncthreads_or(!ok)) {
@@ -1181,45 +1305,45 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : GD_LEAF_MIN_C
         return;
       }
       phase ^= 1u;
-      process_leaf<KMAX, uint16_t, kRec>(A, lf, s_pts, Ms, S);
+      process_leaf<KMAX, uint16_t, kRec, kXl>(A, lf, s_pts, Ms, S);
     } else {
       LeafMem Mg;
       carve<uint32_t>(A.big_scratch + (size_t)lf.start * A.big_bpp, lf.count, KMAX, &Mg);
       Mg.pend = Ms.pend;  // the per-query parked keys live in shared memory on this path too
-      process_leaf<KMAX, uint32_t, kRec>(A, lf, A.spts + lf.start, Mg, S);
+      process_leaf<KMAX, uint32_t, kRec, kXl>(A, lf, A.spts + lf.start, Mg, S);
     }
     __syncthreads();
   }
 }
 
-template <int KMAX, bool kRec>
+template <int KMAX, bool kRec, bool kXl>
 inline int launch_k(const LeafArgs &a, int num_sms, cudaStream_t st) {
   const size_t smem = leaf_smem_bytes(a.lmax, KMAX);
   // per call (function attributes are per device, and calls may come from several threads)
-  if (cudaFuncSetAttribute(k_leaf<KMAX, kRec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(k_leaf<KMAX, kRec, kXl>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return -1;
-  cudaFuncSetAttribute(k_leaf<KMAX, kRec>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  cudaFuncSetAttribute(k_leaf<KMAX, kRec, kXl>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        (int)cudaSharedmemCarveoutMaxShared);
   const int nt = (a.threads == 64) ? 64 : kLeafThreads;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf<KMAX, kRec>, nt, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf<KMAX, kRec, kXl>, nt, smem) != cudaSuccess ||
       per_sm < 1)
     return -1;
   if (a.ctas_per_sm > 0 && (int)a.ctas_per_sm < per_sm) per_sm = (int)a.ctas_per_sm;
   LeafArgs la = a;
   if (la.spin_limit == 0) la.spin_limit = kSpinLimit;
-  if (launch_pdl(k_leaf<KMAX, kRec>, num_sms * per_sm, nt, smem, st, la) != cudaSuccess) return -1;
+  if (launch_pdl(k_leaf<KMAX, kRec, kXl>, num_sms * per_sm, nt, smem, st, la) != cudaSuccess) return -1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <bool kRec>
+template <bool kRec, bool kXl>
 inline int launch_kmax(const LeafArgs &a, int num_sms, cudaStream_t st) {
   switch (leaf_kmax(a.p.k)) {
-    case 8: return launch_k<8, kRec>(a, num_sms, st);
-    case 16: return launch_k<16, kRec>(a, num_sms, st);
-    case 32: return launch_k<32, kRec>(a, num_sms, st);
-    default: return launch_k<64, kRec>(a, num_sms, st);
+    case 8: return launch_k<8, kRec, kXl>(a, num_sms, st);
+    case 16: return launch_k<16, kRec, kXl>(a, num_sms, st);
+    case 32: return launch_k<32, kRec, kXl>(a, num_sms, st);
+    default: return launch_k<64, kRec, kXl>(a, num_sms, st);
   }
 }
 

@@ -4,6 +4,6 @@
 
 namespace gd {
 
-int launch_leaf_rec(const LeafArgs &a, int num_sms, cudaStream_t st) { return launch_kmax<true>(a, num_sms, st); }
+int launch_leaf_rec(const LeafArgs &a, int num_sms, cudaStream_t st) { return launch_kmax<true, false>(a, num_sms, st); }
 
 }  // namespace gd

@@ -118,6 +118,12 @@ extern "C" int denoise_run_noalloc(const float *xyz, size_t n, const denoise_par
   if ((mask && !dev_ptr(mask, dev)) || (score && !dev_ptr(score, dev)) || (stage && !dev_ptr(stage, dev)))
     return DENOISE_E_INVAL;
   if (leaf_big_bpp(64) > kSpillBpp) return DENOISE_E_INVAL;  // carve no longer covers the spill stride
+  {
+    // the call reads the device status back, which a capturing stream cannot do
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) return fail_cuda();
+    if (cs != cudaStreamCaptureStatusNone) return DENOISE_E_INVAL;
+  }
   DeviceSetup su;
   {
     std::lock_guard<std::mutex> lock(g_setup_mu);
