@@ -396,10 +396,11 @@ def run_ours(args):
     xu_peak = props.multi_processor_count * XU_PER_SM_CLK * sm_mhz * 1e6 / 1e12
     xu_ops = stats["score_terms"] * XU_OPS_PER_TERM
     noscore_ms = sum(leaf_ms_noscore) / len(leaf_ms_noscore)
-    score_phase_ms = max(leaf_avg_ms - noscore_ms, 1e-6)
-    xu_achieved = xu_ops / (score_phase_ms / 1000.0) / 1e12
+    score_phase_ms = leaf_avg_ms - noscore_ms
+    # (a difference lost in the timing noise -- as under a profiler -- gives no figure)
+    xu_achieved = xu_ops / (score_phase_ms / 1000.0) / 1e12 if score_phase_ms > 0.02 * leaf_avg_ms else None
     roofline_score = {"bound": "xu", "achieved": xu_achieved, "peak": xu_peak, "unit": "Tops/s",
-                      "frac": xu_achieved / xu_peak,
+                      "frac": xu_achieved / xu_peak if xu_achieved is not None else None,
                       "work": f"{stats['score_terms']} neighbour terms x {XU_OPS_PER_TERM:g} SFU ops (ex2, rcp)",
                       "time_basis": "score + selection phases: leaf kernel with the score stage minus without it",
                       "score_phase_ms": score_phase_ms, "leaf_kernel_ms_score_off": noscore_ms,

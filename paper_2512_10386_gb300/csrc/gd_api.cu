@@ -237,6 +237,7 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
   fa.dbg_key = dbg ? dbg->key : nullptr;
   fa.max_depth = (int)p.max_depth;
   fa.leaf_capacity = p.leaf_capacity;
+  fa.full_sort = p.cross_leaf != 0;
   fa.spin_limit = c->wait_limit;
   fa.hold_tile1 = c->hold_tile1;
   if (launch_front(fa, st, &launches, use_events ? &c->ev[1] : nullptr, use_events ? &c->ev[2] : nullptr))
@@ -287,7 +288,7 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
     XleafArgs xa{};
     xa.n = n;
     xa.spts = c->d_spts;
-    xa.keys = c->d_keys[front_passes((int)p.max_depth) & 1];
+    xa.keys = c->d_keys[front_sorted_buffer((int)p.max_depth, true)];
     xa.leaves = c->d_leaves;
     xa.frames = c->d_frames;
     xa.ctr = c->d_ctr;

@@ -16,6 +16,10 @@ constexpr int kFrontItems = kTilePts / kFrontThreads; // 8
 static_assert(kFrontThreads == 256, "the radix pass maps one thread to each 8-bit digit");
 static_assert(kTilePts % kFrontThreads == 0, "whole items per thread");
 constexpr int kMaxPasses = 8;                         // 8-bit radix digits over <= 63 key bits
+// The radix sort runs over the top key bits only (at most kTopPasses digits: the
+// octree down to some level DB); below DB the full order is only needed inside the
+// level-DB nodes that hold more than leaf_capacity points, sorted one by one.
+constexpr int kTopPasses = 4;
 constexpr uint32_t kSpinLimit = 1u << 22;             // bounded device-side waits
 
 // device status word bits
@@ -163,9 +167,11 @@ struct FrontArgs {
   uint32_t leaf_capacity;
   uint32_t spin_limit;      // iterations of a bounded look-back wait (0 = kSpinLimit)
   uint32_t hold_tile1;      // test hook: tile hold_tile1 - 1 of the first radix pass never publishes (0 = off)
+  bool full_sort;           // sort by every key bit (the cross-leaf variant searches cells of any level)
 };
 
-int front_passes(int max_depth);
+// Which of the two key buffers holds the sorted keys after launch_front.
+int front_sorted_buffer(int max_depth, bool full_sort);
 int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t *ev_after_keys,
                  cudaEvent_t *ev_after_sort);
 

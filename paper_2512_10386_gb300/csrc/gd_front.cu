@@ -3,7 +3,8 @@
 // and the octree leaf finder (leaf = shallowest node holding <= leaf_capacity
 // points, or a node at max_depth).
 //
-// Radix sort design (one kernel per 8-bit digit pass): a tile of 2,048 keys is
+// Radix sort design (one kernel per 8-bit digit pass, over the top key bits
+// only -- see k_node_sort for the rest): a tile of 2,048 keys is
 // ranked stably inside the block with warp match_any, per-digit tile counts are
 // published to a look-back array and each tile's exclusive prefix is built by
 // decoupled look-back over earlier tiles of the same frame (bounded spins), on
@@ -364,6 +365,180 @@ __global__ void __launch_bounds__(kFrontThreads) k_radix_pass(
   }
 }
 
+// ---------------------------------------------------------------------------
+// Order inside the nodes that need it.  The radix passes sort by the key bits
+// from `lowbit` up, which places every octree node down to level DB (the sorted
+// depth) in one contiguous range; inside a level-DB node the points keep their
+// input order.  That is all the leaf partition needs wherever a level-DB node
+// holds at most leaf_capacity points (it lies inside one leaf).  A level-DB node
+// with more points ("big") is brought into the full order here, (key bits from
+// key_low up, input index), by the block of the tile where it starts: in shared
+// memory (bitonic network) up to kNodeSmem points, else by stable 8-bit passes
+// through the other key buffer.  Its packed points are written again after.
+// (The point indices are taken from the packed points: the last radix pass
+// writes them there instead of into the value buffer.)
+// ---------------------------------------------------------------------------
+constexpr uint32_t kNodeSmem = 2048;
+
+__device__ __forceinline__ bool node_less(unsigned long long ka, uint32_t va, unsigned long long kb, uint32_t vb,
+                                          int key_low) {
+  const unsigned long long a = ka >> key_low, b = kb >> key_low;
+  return a < b || (a == b && va < vb);
+}
+
+__global__ void __launch_bounds__(kFrontThreads) k_node_sort(
+    unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals, unsigned long long *__restrict__ tmpk,
+    uint32_t *__restrict__ tmpv, float4 *__restrict__ spts, const float *__restrict__ xyz,
+    const Tile *__restrict__ tiles, const FrameInfo *__restrict__ frames, Counters *ctr, uint32_t cap, int DB,
+    int key_low) {
+  constexpr int W = kFrontThreads / 32;
+  __shared__ unsigned long long s_k[kNodeSmem];
+  __shared__ uint32_t s_v[kNodeSmem];
+  __shared__ uint32_t s_start[kTilePts];
+  __shared__ uint32_t s_off[256];
+  __shared__ uint32_t s_wc[W][256];
+  __shared__ uint32_t s_wsum[W];
+  __shared__ uint32_t s_n, s_end;
+  pdl_wait();
+  if (ctr->status & kStFatal) return;
+  const Tile t = tiles[blockIdx.x];
+  const uint32_t fb = frames[t.frame].begin, fe = frames[t.frame].end;
+  const int sh = 63 - 3 * DB;  // a level-DB node's keys share key >> sh
+  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) s_n = 0;
+  __syncthreads();
+  // the big nodes that start in this tile
+  for (uint32_t i = t.begin + tid; i < t.end; i += kFrontThreads) {
+    const unsigned long long pre = keys[i] >> sh;
+    const bool first = (i == fb) || ((keys[i - 1] >> sh) != pre);
+    if (first && fe - i > cap && (keys[i + cap] >> sh) == pre) s_start[atomicAdd(&s_n, 1u)] = i;
+  }
+  __syncthreads();
+  const uint32_t nn = s_n;
+  for (uint32_t u = 0; u < nn; ++u) {
+    const uint32_t s = s_start[u];
+    if (tid == 0) {  // the node's end: it holds more than cap points, all sharing the prefix
+      const unsigned long long pre = keys[s] >> sh;
+      uint32_t lo = s + cap, hi = fe;
+      while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if ((keys[mid] >> sh) == pre) lo = mid + 1;
+        else hi = mid;
+      }
+      s_end = lo;
+    }
+    __syncthreads();
+    const uint32_t e = s_end, n = e - s;
+    // the last radix pass leaves the point indices in the packed points, not in vals
+    for (uint32_t i = s + tid; i < e; i += kFrontThreads) vals[i] = __float_as_uint(spts[i].w);
+    __syncthreads();
+    if (n <= kNodeSmem) {
+      uint32_t n2 = 1;
+      while (n2 < n) n2 <<= 1;
+      for (uint32_t j = tid; j < n2; j += kFrontThreads) {
+        s_k[j] = j < n ? keys[s + j] : ~0ull;  // padding sorts last
+        s_v[j] = j < n ? vals[s + j] : 0xFFFFFFFFu;
+      }
+      __syncthreads();
+      for (uint32_t size = 2; size <= n2; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+          for (uint32_t c = tid; c < (n2 >> 1); c += kFrontThreads) {
+            const uint32_t a = 2 * stride * (c / stride) + (c % stride), b = a + stride;
+            const bool up = (a & size) == 0;
+            const unsigned long long ka = s_k[a], kb = s_k[b];
+            const uint32_t va = s_v[a], vb = s_v[b];
+            if (node_less(kb, vb, ka, va, key_low) == up) {
+              s_k[a] = kb;
+              s_k[b] = ka;
+              s_v[a] = vb;
+              s_v[b] = va;
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (uint32_t j = tid; j < n; j += kFrontThreads) {
+        keys[s + j] = s_k[j];
+        vals[s + j] = s_v[j];
+      }
+    } else {
+      // stable passes over the digits below the shared prefix, lowest first
+      for (uint32_t i = tid; i < W * 256; i += kFrontThreads) (&s_wc[0][0])[i] = 0;
+      unsigned long long *sk = keys, *dk = tmpk;
+      uint32_t *sv = vals, *dv = tmpv;
+      for (int shift = key_low; shift < sh; shift += 8) {
+        s_off[tid] = 0;  // one digit per thread (kFrontThreads == 256)
+        __syncthreads();
+        for (uint32_t i = s + tid; i < e; i += kFrontThreads) atomicAdd(&s_off[(uint32_t)(sk[i] >> shift) & 0xFFu], 1u);
+        __syncthreads();
+        {  // exclusive scan of the 256 counts, offset by the node's start
+          const uint32_t v = s_off[tid];
+          uint32_t x = v;
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+          }
+          if (lane == 31) s_wsum[w] = x;
+          __syncthreads();
+          uint32_t wp = 0;
+          for (uint32_t ww = 0; ww < w; ++ww) wp += s_wsum[ww];
+          s_off[tid] = s + wp + x - v;
+        }
+        __syncthreads();
+        const uint32_t lt = lanemask_lt();
+        for (uint32_t c0 = s; c0 < e; c0 += kFrontThreads) {
+          const uint32_t i = c0 + tid;
+          const bool ok = i < e;
+          const unsigned long long k = ok ? sk[i] : 0ull;
+          const uint32_t v = ok ? sv[i] : 0u;
+          const uint32_t d = ok ? ((uint32_t)(k >> shift) & 0xFFu) : 256u;
+          const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+          if (ok && (peers & lt) == 0) s_wc[w][d] = __popc(peers);
+          __syncthreads();
+          if (ok) {
+            uint32_t pos = s_off[d] + __popc(peers & lt);
+            for (uint32_t ww = 0; ww < w; ++ww) pos += s_wc[ww][d];
+            dk[pos] = k;
+            dv[pos] = v;
+          }
+          __syncthreads();
+          {  // digit tid: advance its offset by the chunk's count, clear the warp counts
+            uint32_t tot = 0;
+            for (int ww = 0; ww < W; ++ww) {
+              tot += s_wc[ww][tid];
+              s_wc[ww][tid] = 0;
+            }
+            s_off[tid] += tot;
+          }
+          __syncthreads();
+        }
+        unsigned long long *tk = sk;
+        sk = dk;
+        dk = tk;
+        uint32_t *tv = sv;
+        sv = dv;
+        dv = tv;
+      }
+      if (sk != keys) {  // an odd number of passes: the result is in the other buffer
+        for (uint32_t i = s + tid; i < e; i += kFrontThreads) {
+          keys[i] = sk[i];
+          vals[i] = sv[i];
+        }
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = s + tid; i < e; i += kFrontThreads) {
+      const uint32_t v = vals[i];
+      if (v >= fe) {  // values are point indices of this batch
+        atomicOr(&ctr->status, kStInternal);
+        continue;
+      }
+      spts[i] = make_float4(xyz[3ull * v], xyz[3ull * v + 1], xyz[3ull * v + 2], __uint_as_float(v));
+    }
+    __syncthreads();
+  }
+}
+
 // Without a sort (max_depth 0: one leaf per frame) the points are packed as is.
 __global__ void k_pack(const float *__restrict__ xyz, const Tile *__restrict__ tiles,
                        float4 *__restrict__ pout, const Counters *ctr) {
@@ -429,7 +604,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
                                                           const Tile *__restrict__ tiles,
                                                           const FrameInfo *__restrict__ frames,
                                                           Leaf *__restrict__ leaves, Counters *ctr,
-                                                          uint32_t cap, int D) {
+                                                          uint32_t cap, int D, int DB) {
   extern __shared__ unsigned long long s_win[];
   pdl_wait();
   if (ctr->status & kStFatal) return;
@@ -468,6 +643,15 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
       const unsigned long long x = kb[i - 1 - koff] ^ ki;
       int l = (x == 0) ? 21 : (__clzll((long long)x) - 1) / 3;  // shared levels below the root
       if (l >= D) continue;                                      // same max-depth node
+      if (l > DB) {
+        // i-1 and i share a level-DB node; below level DB the keys are in octree
+        // order only inside level-DB nodes of more than cap points.  A smaller one
+        // lies inside one leaf, which cannot start at i.
+        const unsigned long long preB = prefix_of(ki, DB);
+        const uint32_t wlo = (i - fb > cap + 1) ? i - cap - 1 : fb;
+        const uint32_t whi = (fe - i > cap + 1) ? i + cap + 1 : fe;
+        if (upper_pre(kb, koff, i, whi, preB, DB) - lower_pre(kb, koff, wlo, i, preB, DB) <= cap) continue;
+      }
       // count of the level-l node containing i-1 and i, decided within a window
       bool big;
       if (l == 0) {
@@ -535,12 +719,29 @@ __global__ void __launch_bounds__(kFrontThreads) k_leaves(const unsigned long lo
 // ---------------------------------------------------------------------------
 // host launcher
 // ---------------------------------------------------------------------------
-int front_passes(int max_depth) { return (3 * max_depth + 7) / 8; }
+namespace {
+// The passes of a call: all ceil(3 D / 8) digits of the key's 3 D bits, or the top
+// kTopPasses of them; *sorted_depth receives the deepest level whose nodes are
+// contiguous after them (D when every bit is sorted), *key_low the key's lowest bit.
+int front_plan(int max_depth, bool full_sort, int *lowbit, int *sorted_depth, int *key_low) {
+  const int all = (3 * max_depth + 7) / 8;
+  const int passes = (full_sort || all <= kTopPasses) ? all : kTopPasses;
+  *key_low = 63 - 3 * max_depth;
+  *lowbit = *key_low + 8 * (all - passes);  // lowest sorted bit
+  *sorted_depth = (passes == all) ? max_depth : (63 - *lowbit) / 3;
+  return passes;
+}
+}  // namespace
+
+int front_sorted_buffer(int max_depth, bool full_sort) {
+  int lowbit, db, kl;
+  return front_plan(max_depth, full_sort, &lowbit, &db, &kl) & 1;
+}
 
 int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t *ev_after_keys,
                  cudaEvent_t *ev_after_sort) {
-  const int passes = front_passes(a.max_depth);
-  const int lowbit = 63 - 3 * a.max_depth;
+  int lowbit = 0, DB = 0, key_low = 0;
+  const int passes = front_plan(a.max_depth, a.full_sort, &lowbit, &DB, &key_low);
   const uint32_t spin = a.spin_limit ? a.spin_limit : kSpinLimit;
   const uint32_t nlb = a.ntiles * 256u;
   int nl = 0;
@@ -583,15 +784,20 @@ int launch_front(const FrontArgs &a, cudaStream_t st, int *launches, cudaEvent_t
     launch_pdl(k_pack, a.ntiles, kFrontThreads, 0, st, a.xyz, a.tiles, a.spts, a.ctr);
     ++nl;
   }
+  // a capacity above any frame's size means the same as "the root is a leaf"; clamped
+  // so that the finder's window arithmetic (cap + 1) cannot wrap
+  const uint32_t cap = a.leaf_capacity < (1u << 30) ? a.leaf_capacity : (1u << 30);
+  if (DB < a.max_depth) {  // the big level-DB nodes in full octree order
+    launch_pdl(k_node_sort, a.ntiles, kFrontThreads, 0, st, a.keys[cur], a.vals[cur], a.keys[cur ^ 1], a.vals[cur ^ 1],
+               a.spts, a.xyz, a.tiles, a.frames, a.ctr, cap, DB, key_low);
+    ++nl;
+  }
   if (ev_after_sort) cudaEventRecord(*ev_after_sort, st);
   const size_t win = (a.leaf_capacity <= kLeavesSmemCap)
                         ? sizeof(unsigned long long) * (kLeavesPart + 2 * ((size_t)a.leaf_capacity + 1))
                         : 0;
-  // a capacity above any frame's size means the same as "the root is a leaf"; clamped
-  // so that the finder's window arithmetic (cap + 1) cannot wrap
-  const uint32_t cap = a.leaf_capacity < (1u << 30) ? a.leaf_capacity : (1u << 30);
   launch_pdl(k_leaves, a.ntiles * kLeavesSplit, kFrontThreads, win, st, a.keys[cur], a.tiles, a.frames, a.leaves, a.ctr,
-             cap, a.max_depth);
+             cap, a.max_depth, DB);
   ++nl;
   if (launches) *launches += nl;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -372,6 +372,18 @@ __device__ __forceinline__ void regsort_u(uint32_t (&L)[N]) {
     L[net.b[c]] = umax(x, y);
   }
 }
+// the same on the first H entries of L (the rest already sorted and not below them)
+template <int H, int N>
+__device__ __forceinline__ void regsort_head(uint32_t (&L)[N]) {
+  static_assert(H <= N, "head within the array");
+  constexpr OddEvenNet<H> net{};
+#pragma unroll
+  for (int c = 0; c < OddEvenNet<H>::C; ++c) {
+    const uint32_t x = L[net.a[c]], y = L[net.b[c]];
+    L[net.a[c]] = umin(x, y);
+    L[net.b[c]] = umax(x, y);
+  }
+}
 
 // Lref of the score (Eq. 16-17), from the lower-middle r^2 (ra) and upper-middle
 // r^2 (rb) of P_2's m points.  Once per leaf by one thread: kept out of line.
@@ -407,51 +419,15 @@ __device__ __forceinline__ bool rec_index_ok(const LeafArgs &A, uint32_t g) {
   return false;
 }
 
-// L2 eviction policies.  The leaf's packed points are read once (evict first);
-// the outputs are written by input index, so a 32-byte sector of them is
-// completed by several leaves at different times: kept in L2 (evict last) a
-// sector is merged there, evicted half written it costs a DRAM read-modify-write.
-#ifndef GD_SCORE_CHAINS
-#define GD_SCORE_CHAINS 2
-#endif
-#ifndef GD_LEAF_L2HINT
-#define GD_LEAF_L2HINT 1
-#endif
-__device__ __forceinline__ uint64_t l2_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t l2_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ void st_keep_u8(uint8_t *p, uint32_t v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.u8 [%0], %1, %2;" ::"l"(__cvta_generic_to_global(p)), "r"(v), "l"(pol)
-               : "memory");
-}
-__device__ __forceinline__ void st_keep_f32(float *p, float v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(__cvta_generic_to_global(p)), "f"(v), "l"(pol)
-               : "memory");
-}
-
 template <bool kRec>
 __device__ __forceinline__ void write_point(const LeafArgs &A, uint32_t g, uint8_t mk, float sc, uint8_t st) {
   if (g >= A.n) {  // cannot happen with a consistent sort; never write out of bounds
     atomicOr(&A.ctr->status, kStInternal);
     return;
   }
-#if GD_LEAF_L2HINT
-  const uint64_t pol = l2_evict_last();
-  if (A.mask) st_keep_u8(A.mask + g, mk, pol);
-  if (A.score) st_keep_f32(A.score + g, sc, pol);
-  if (A.stage) st_keep_u8(A.stage + g, st, pol);
-#else
   if (A.mask) A.mask[g] = mk;
   if (A.score) A.score[g] = sc;
   if (A.stage) A.stage[g] = st;
-#endif
   if (kRec && A.use_train) {
     A.train.stage[g] = st;
     A.train.F[g] = sc;
@@ -1129,26 +1105,6 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         M.F[i] = __fadd_rn(F0, F1);
         continue;
       }
-#if GD_SCORE_CHAINS == 4
-      // four ranks per step (four independent chains, rank t into sum t mod 4);
-      // missing ranks of the last step are computed on the first neighbour again and dropped
-      float F2 = 0.0f, F3 = 0.0f;
-#pragma unroll 1
-      for (uint32_t t = 0; t < keff; t += 4) {
-        const bool v1 = t + 1 < keff, v2 = t + 2 < keff, v3 = t + 3 < keff;
-        const uint32_t ja = next_j(t, true);
-        uint32_t jb = next_j(t + 1, v1), jc = next_j(t + 2, v2), jd = next_j(t + 3, v3);
-        jb = v1 ? jb : ja;
-        jc = v2 ? jc : ja;
-        jd = v3 ? jd : ja;
-        const float e0 = term(ja), e1 = term(jb), e2 = term(jc), e3 = term(jd);
-        F0 = __fadd_rn(F0, e0);
-        if (v1) F1 = __fadd_rn(F1, e1);
-        if (v2) F2 = __fadd_rn(F2, e2);
-        if (v3) F3 = __fadd_rn(F3, e3);
-      }
-      M.F[i] = __fadd_rn(__fadd_rn(F0, F1), __fadd_rn(F2, F3));
-#else
       // two ranks per step (two independent chains); with k_eff odd the last step's
       // second term is computed on the first neighbour again and dropped
 #pragma unroll 1
@@ -1162,7 +1118,6 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         if (two) F1 = __fadd_rn(F1, e1);
       }
       M.F[i] = __fadd_rn(F0, F1);
-#endif
     }
   }
   __syncthreads();
@@ -1285,18 +1240,10 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : GD_LEAF_MIN_C
         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s_pts);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-#if GD_LEAF_L2HINT
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
-            "%4;" ::"r"(dst),
-            "l"(__cvta_generic_to_global(A.spts + lf.start)), "r"(bytes), "r"(bar), "l"(l2_evict_first())
-            : "memory");
-#else
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
             "l"(__cvta_generic_to_global(A.spts + lf.start)), "r"(bytes), "r"(bar)
             : "memory");
-#endif
       }
       const bool ok = mbar_wait(bar, phase, A.spin_limit);
       if (__syncthreads_or(!ok)) {

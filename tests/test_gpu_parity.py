@@ -101,6 +101,23 @@ def test_duplicates_and_oversized_leaf(dn, orc):
     compare_with_oracle(g, r, P)
 
 
+@pytest.mark.parametrize("n_cluster", [1500, 5000])
+def test_dense_cluster_below_sorted_depth(dn, orc, n_cluster):
+    """A cluster far smaller than a level-10 cell of the root cube: its leaves lie
+    deeper than the levels the radix passes order, so its cell is brought into full
+    octree order on its own (in shared memory up to 2,048 points, else by digit
+    passes); with identical points too."""
+    rng = np.random.default_rng(n_cluster)
+    rest = rng.uniform(-1, 1, size=(4000, 3)).astype(np.float32)
+    cl = (np.float32([0.3, -0.2, 0.1]) + rng.uniform(0, 1e-4, size=(n_cluster, 3))).astype(np.float32)
+    dup = np.repeat(np.float32([[-0.6, 0.4, 0.7]]), n_cluster // 2, axis=0)
+    xyz = np.concatenate([rest[:1000], cl[: n_cluster // 2], dup, rest[1000:], cl[n_cluster // 2:]])
+    P = P_(k=16, leaf_capacity=64, min_vox_count=1)
+    g, r = run_both(dn, orc, xyz, P)
+    assert r["leaf_level"].max() > 10
+    compare_with_oracle(g, r, P)
+
+
 def test_shallow_octree_large_leaves(dn, orc):
     import synth
     xyz, _ = synth.object_cloud(seed=7, n_surface=6000)
