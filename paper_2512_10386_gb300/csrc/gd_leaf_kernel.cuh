@@ -802,7 +802,10 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
 #pragma unroll
         for (int i = 0; i < (int)kSelBuf; ++i)
           K[i] = (parked && (uint32_t)i < np) ? pend[i * kLeafThreads + tid] : 0xFFFFFFFFu;
-        regsort_u<kSelBuf>(K);
+        // with at most 8 parked keys in every lane of the warp (the usual case) the
+        // padding keys above them stay in place: a network on the first 8 suffices
+        if (__reduce_max_sync(0xFFFFFFFFu, parked ? np : 0u) <= kSelBuf / 2) regsort_head<kSelBuf / 2>(K);
+        else regsort_u<kSelBuf>(K);
         uint32_t th_off = 0;
 #pragma unroll
         for (int i = 0; i < (int)kSelBuf; ++i) {
