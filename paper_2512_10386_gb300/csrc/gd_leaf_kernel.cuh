@@ -1012,7 +1012,11 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
     for (uint32_t i = tid; i < n1; i += NT) {
       const float r2 = M.r2[i];
       const float ell = __fsub_rn(Lref, __fmul_rn(1.5f, log2f(__fdiv_rn(r2, r2ref))));  // log2(rho_i / sqrt(rho_med^2 + eps))
-      M.wa[i] = __fmul_rn(half_alpha, ell);
+      const float wa = __fmul_rn(half_alpha, ell);
+      M.wa[i] = wa;
+      // shared-memory leaves: each point's (x, y, z, weight) in one 16-byte word for
+      // the score's neighbour reads (region R is idle between the median and Top-lambda)
+      if constexpr (kPacked) reinterpret_cast<float4 *>(M.sbuf)[i] = make_float4(X[i], Y[i], Z[i], wa);
       if (kRec && A.use_train) {
         const uint32_t g = W[i];
         if (rec_index_ok(A, g)) A.train.ell[g] = ell;
@@ -1081,8 +1085,21 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         }
       };
       auto term = [&](uint32_t j) {
-        const float d2 = sqdist(xi, yi, zi, X[j], Y[j], Z[j]);
-        const float wt = ex2_hw(__fmaf_rn(-d2, ci, __fadd_rn(ai, M.wa[j])));  // w_den * w_dis (Eq. 17, 19)
+        float xj, yj, zj, aj;
+        if constexpr (kPacked) {
+          const float4 pj = reinterpret_cast<const float4 *>(M.sbuf)[j];
+          xj = pj.x;
+          yj = pj.y;
+          zj = pj.z;
+          aj = pj.w;
+        } else {
+          xj = X[j];
+          yj = Y[j];
+          zj = Z[j];
+          aj = M.wa[j];
+        }
+        const float d2 = sqdist(xi, yi, zi, xj, yj, zj);
+        const float wt = ex2_hw(__fmaf_rn(-d2, ci, __fadd_rn(ai, aj)));  // w_den * w_dis (Eq. 17, 19)
         const float D = g2 ? d2 : pow_half_gamma(d2, hg);                    // (d^2)^(gamma/2)
         return __fmul_rn(wt, rcp_hw(__fadd_rn(D, ek)));                    // kernel of Eq. 20
       };
