@@ -8,8 +8,8 @@ namespace gd {
 
 // Packed two-lane FP32 (sm_100 family): each instruction applies the same
 // round-to-nearest operation to both halves of a 64-bit register pair, with
-// subnormals kept, so a lane of the pair equals the scalar __fsub_rn /
-// __fmul_rn / __fmaf_rn bit for bit.
+// subnormals kept, so a lane of the pair equals the scalar __fadd_rn /
+// __fsub_rn / __fmul_rn / __fmaf_rn bit for bit.
 typedef unsigned long long f32x2;
 __device__ __forceinline__ f32x2 pk2(float lo, float hi) {
   f32x2 r;
@@ -22,6 +22,11 @@ __device__ __forceinline__ void upk2(f32x2 v, float &lo, float &hi) {
 __device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
   f32x2 r;
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
 }
 __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {

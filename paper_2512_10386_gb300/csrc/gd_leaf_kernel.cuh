@@ -1084,25 +1084,6 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           return valid ? (uint32_t)nbr[(size_t)t * M.cap + i] : 0u;
         }
       };
-      auto term = [&](uint32_t j) {
-        float xj, yj, zj, aj;
-        if constexpr (kPacked) {
-          const float4 pj = reinterpret_cast<const float4 *>(M.sbuf)[j];
-          xj = pj.x;
-          yj = pj.y;
-          zj = pj.z;
-          aj = pj.w;
-        } else {
-          xj = X[j];
-          yj = Y[j];
-          zj = Z[j];
-          aj = M.wa[j];
-        }
-        const float d2 = sqdist(xi, yi, zi, xj, yj, zj);
-        const float wt = ex2_hw(__fmaf_rn(-d2, ci, __fadd_rn(ai, aj)));  // w_den * w_dis (Eq. 17, 19)
-        const float D = g2 ? d2 : pow_half_gamma(d2, hg);                    // (d^2)^(gamma/2)
-        return __fmul_rn(wt, rcp_hw(__fadd_rn(D, ek)));                    // kernel of Eq. 20
-      };
       if (xl) {
         // cross-leaf neighbours: coordinates and densities from the global results,
         // ell_j = log2(rho_j) - lshift with rho_j from the neighbour's own k_eff and r_K
@@ -1125,18 +1106,40 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
         M.F[i] = __fadd_rn(F0, F1);
         continue;
       }
-      // two ranks per step (two independent chains); with k_eff odd the last step's
-      // second term is computed on the first neighbour again and dropped
+      // two ranks per step in the two lanes of packed FP32 instructions (even ranks
+      // in the low lane, odd in the high: the two partial sums); each lane rounds as
+      // the scalar form.  With k_eff odd the last step's second term is computed on
+      // the first neighbour again and replaced by +0.
+      const f32x2 XI = pk2(xi, xi), YI = pk2(yi, yi), ZI = pk2(zi, zi), AI = pk2(ai, ai);
+      const f32x2 NCI = pk2(-ci, -ci), EK = pk2(ek, ek);
+      f32x2 FF = pk2(0.0f, 0.0f);
 #pragma unroll 1
       for (uint32_t t = 0; t < keff; t += 2) {
         const bool two = t + 1 < keff;
         const uint32_t ja = next_j(t, true);
         uint32_t jb = next_j(t + 1, two);
         jb = two ? jb : ja;
-        const float e0 = term(ja), e1 = term(jb);
-        F0 = __fadd_rn(F0, e0);
-        if (two) F1 = __fadd_rn(F1, e1);
+        float4 pa, pb;
+        if constexpr (kPacked) {
+          pa = reinterpret_cast<const float4 *>(M.sbuf)[ja];
+          pb = reinterpret_cast<const float4 *>(M.sbuf)[jb];
+        } else {
+          pa = make_float4(X[ja], Y[ja], Z[ja], M.wa[ja]);
+          pb = make_float4(X[jb], Y[jb], Z[jb], M.wa[jb]);
+        }
+        const f32x2 DX = sub2(pk2(pa.x, pb.x), XI), DY = sub2(pk2(pa.y, pb.y), YI), DZ = sub2(pk2(pa.z, pb.z), ZI);
+        const f32x2 D2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
+        float ea, eb, da, db;
+        upk2(fma2(D2, NCI, add2(AI, pk2(pa.w, pb.w))), ea, eb);  // -d^2 c_i + (alpha/2)(ell_i + ell_j)
+        upk2(D2, da, db);
+        const f32x2 DG = g2 ? D2 : pk2(pow_half_gamma(da, hg), pow_half_gamma(db, hg));
+        float qa, qb;
+        upk2(add2(DG, EK), qa, qb);
+        float ta, tb;
+        upk2(mul2(pk2(ex2_hw(ea), ex2_hw(eb)), pk2(rcp_hw(qa), rcp_hw(qb))), ta, tb);
+        FF = add2(FF, pk2(ta, two ? tb : 0.0f));
       }
+      upk2(FF, F0, F1);
       M.F[i] = __fadd_rn(F0, F1);
     }
   }
