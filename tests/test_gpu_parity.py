@@ -118,6 +118,21 @@ def test_dense_cluster_below_sorted_depth(dn, orc, n_cluster):
     compare_with_oracle(g, r, P)
 
 
+@pytest.mark.parametrize("max_depth", [12, 15])
+def test_cluster_below_sorted_depth_limited_depth(dn, orc, max_depth):
+    """As above with a depth limit below 21: the sorted key bits start above bit 0
+    and the cells needing full order are sorted by the key bits the limit keeps
+    (ties in them by input index)."""
+    rng = np.random.default_rng(max_depth)
+    rest = rng.uniform(-1, 1, size=(3000, 3)).astype(np.float32)
+    cl = (np.float32([0.3, -0.2, 0.1]) + rng.uniform(0, 3e-4, size=(2600, 3))).astype(np.float32)
+    xyz = np.concatenate([rest[:1000], cl, rest[1000:]])
+    P = P_(k=16, leaf_capacity=48, max_depth=max_depth, min_vox_count=1)
+    g, r = run_both(dn, orc, xyz, P)
+    assert r["leaf_level"].max() > 9
+    compare_with_oracle(g, r, P)
+
+
 def test_shallow_octree_large_leaves(dn, orc):
     import synth
     xyz, _ = synth.object_cloud(seed=7, n_surface=6000)
