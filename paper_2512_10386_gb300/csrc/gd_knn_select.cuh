@@ -35,7 +35,7 @@
 namespace gd {
 
 constexpr int kSelBuckets = 32;
-constexpr int kSelS0 = 21;          // first-level bucket width: 2^21 patterns = a quarter octave of d^2
+constexpr int kSelS0 = 20;          // first-level bucket width: 2^20 patterns = an eighth of an octave of d^2
 constexpr uint32_t kSelBuf = 16;    // parked boundary-bucket candidates per query
 constexpr int kSelMaxLevels = 12;   // refinement levels before a consistency failure is reported
 
@@ -118,6 +118,7 @@ struct SelLevel {
   int32_t lo;        // exclusive bottom bits (-1: none; then the query itself, d^2 = 0, is counted)
   int32_t S;         // bucket width 2^S
   uint32_t c_base;   // neighbours below `lo` (found at earlier levels)
+  int32_t slides;    // catch-all refinements taken at the first level's resolution so far
 };
 
 // Result of the walk: bucket B's range and counts.
@@ -169,15 +170,26 @@ __host__ __device__ __forceinline__ int32_t sel_bitlen(uint32_t v) {
 // range (lo, hi].  For an ordinary bucket (2^S patterns) the width is 2^(S-5);
 // the catch-all last bucket of a level that reaches down to 0 can be wider, and
 // its width is then taken from the range itself.  Either way the largest offset
-// in the range loses at least 5 bits per level.
+// in the range loses at least 5 bits per level.  The exception: the catch-all
+// of a level that reaches down to 0 is first searched (up to kSelSlides times)
+// by the next 31 buckets below it at the same width, with a new catch-all under
+// them -- the k-th distance is then usually a few octaves below the bound, and
+// the boundary bucket comes out narrow at once (split by range, the catch-all's
+// buckets would each span octaves, and take a further level).
+constexpr int32_t kSelSlides = 2;
 __host__ __device__ __forceinline__ SelLevel sel_refine(const SelLevel &L, const SelCut &cut) {
-  (void)L;
   SelLevel n;
   n.tb = cut.hi;
   n.lo = cut.lo;
-  const int32_t nb = sel_bitlen((uint32_t)(cut.hi - cut.lo - 1));  // bits of the largest offset
-  n.S = nb > 5 ? nb - 5 : 0;
   n.c_base = cut.c_below;
+  n.slides = L.slides;
+  if (cut.B == kSelBuckets - 1 && L.lo < 0 && L.slides < kSelSlides) {
+    n.S = L.S;
+    n.slides = L.slides + 1;
+  } else {
+    const int32_t nb = sel_bitlen((uint32_t)(cut.hi - cut.lo - 1));  // bits of the largest offset
+    n.S = nb > 5 ? nb - 5 : 0;
+  }
   return n;
 }
 

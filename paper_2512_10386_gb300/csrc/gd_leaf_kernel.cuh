@@ -603,8 +603,8 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
   // candidates broadcast from shared memory to the warp, four per 16-byte load.
   // The k_eff smallest are found by counting, not by keeping a sorted list
   // (gd_knn_select.cuh): an upper bound theta_0 (the largest d^2 over a window
-  // of Morton neighbours holding k_eff others) fixes 32 buckets of a quarter
-  // octave below it; pass 1 counts every candidate into them (bit-sliced
+  // of Morton neighbours holding k_eff others) fixes 32 buckets of an eighth
+  // of an octave below it; pass 1 counts every candidate into them (bit-sliced
   // counters), which locates the boundary bucket B and the number of
   // neighbours below it; pass 2 emits those neighbours in position order and
   // parks B's few members, which are sorted to finish the set.  A boundary
@@ -649,7 +649,7 @@ __device__ void process_leaf(const LeafArgs &A, const Leaf lf, const float4 *__r
           t0 = fmaxf(fmaxf(t0, d[0]), fmaxf(fmaxf(d[1], d[2]), d[3]));
         }
       }
-      SelLevel L{__float_as_int(t0), -1, kSelS0, 0u};
+      SelLevel L{__float_as_int(t0), -1, kSelS0, 0u, 0};
       SelCut cut;
       {
         // pass 1: every candidate (and the query itself, taken out in the walk) into the buckets

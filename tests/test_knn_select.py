@@ -42,7 +42,7 @@ static bool select(const std::vector<float> &d, const std::vector<uint32_t> &idx
   const int n16 = (n + 15) / 16;
   std::vector<float> dd(n16 * 16, flt(0x7FFFFFFF));          // NaN padding, as in shared memory
   for (int j = 0; j < n; ++j) dd[j] = d[j];
-  SelLevel L{bits(theta0), -1, kSelS0, 0u};
+  SelLevel L{bits(theta0), -1, kSelS0, 0u, 0};
   uint32_t c[PL];
   auto count = [&](bool general) {
     for (int p = 0; p < PL; ++p) c[p] = 0;
