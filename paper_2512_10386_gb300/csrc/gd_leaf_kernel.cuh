@@ -273,29 +273,83 @@ __device__ __forceinline__ void bitonic_sort_regs(T *a, uint32_t n, T pad) {
   __syncthreads();
 }
 
+// The same network on N = 32 * E elements by the first warp alone (small leaves:
+// no block-wide stage, no barrier until the sorted keys are written back).
+template <typename T, int E>
+__device__ __forceinline__ void warp_sort_regs(T *a, uint32_t n, T pad) {
+  if (threadIdx.x < 32) {
+    const uint32_t t = threadIdx.x;
+    T v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const uint32_t e = t * E + k;
+      v[k] = (e < n) ? a[e] : pad;
+    }
+#pragma unroll 1
+    for (uint32_t size = 2; size <= 32u * E; size <<= 1) {
+#pragma unroll 1
+      for (uint32_t j = size >> 1; j > 0; j >>= 1) {
+        if (j < (uint32_t)E) {
+#pragma unroll
+          for (int jj = 1; jj < E; jj <<= 1) {
+            if ((uint32_t)jj != j) continue;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+              const int l = k ^ jj;
+              if (l > k) {
+                const bool asc = ((t * E + k) & size) == 0;
+                const T x = v[k], y = v[l];
+                const T lo = x < y ? x : y, hi = x < y ? y : x;
+                v[k] = asc ? lo : hi;
+                v[l] = asc ? hi : lo;
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < E; ++k) {
+            const uint32_t e = t * E + k;
+            const T y = __shfl_xor_sync(0xFFFFFFFFu, v[k], j / E);
+            const bool take_min = ((e & j) == 0) == ((e & size) == 0);
+            v[k] = take_min ? (v[k] < y ? v[k] : y) : (v[k] < y ? y : v[k]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < E; ++k) a[t * E + k] = v[k];
+  }
+  __syncthreads();
+}
+
 // ascending sort of a[0..n), n a power of two; entries n.. up to the next
 // multiple of blockDim.x (at most 512) may be overwritten with `pad`.  Not inlined:
 // the unrolled networks would otherwise raise the whole kernel's register count.
 template <typename T>
 __device__ __noinline__ void block_sort(T *a, uint32_t n, T pad) {
   const uint32_t nt = blockDim.x;
-  if (n <= nt) bitonic_sort_regs<T, 1>(a, n, pad);
+  // small leaves of 128-thread CTAs: one warp sorts, no block-wide stage (with
+  // 64-thread CTAs the block sort of 64 keys keeps both warps busy and stays faster)
+  if (n <= 32 && nt >= 128) warp_sort_regs<T, 1>(a, n, pad);
+  else if (n <= 64 && nt >= 128) warp_sort_regs<T, 2>(a, n, pad);
+  else if (n <= nt) bitonic_sort_regs<T, 1>(a, n, pad);
   else if (n <= 2 * nt) bitonic_sort_regs<T, 2>(a, n, pad);
   else if (n <= 4 * nt) bitonic_sort_regs<T, 4>(a, n, pad);
   else if (n <= 8 * nt && n <= 512) bitonic_sort_regs<T, 8>(a, n, pad);
   else bitonic_sort_smem<T>(a, n);
 }
 
-// the SFU's exp2 and reciprocal (PTX ex2.approx.f32, rcp.approx.f32: about 2 ulp
-// and 1 ulp, subnormals kept); a score term needs no more than that
+// the SFU's exp2 and reciprocal (PTX ex2.approx.ftz.f32, rcp.approx.ftz.f32: about
+// 2 ulp and 1 ulp; a subnormal argument or result is taken as 0: a score term that
+// small lies below what FP32 resolves in a sum anyway)
 __device__ __forceinline__ float ex2_hw(float x) {
   float y;
-  asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 __device__ __forceinline__ float rcp_hw(float x) {
   float y;
-  asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
