@@ -78,6 +78,9 @@ struct denoise_ctx {
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // graph cache (captured on a private stream, launched on the caller's)
   cudaStream_t cap_stream = nullptr;
+  // the small-leaf launch runs on a side stream, forked from and joined into the call's stream
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<unsigned char> gkey;
   // frame layout cache
@@ -162,6 +165,9 @@ void free_ctx(denoise_ctx *c) {
     if (e) cudaEventDestroy(e);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
   cudaGetLastError();
   delete c;
 }
@@ -305,7 +311,7 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
     ++launches;
     la.xphase = 3;
   }
-  if (launch_leaf(la, c->num_sms, st, &launches)) return cuda_fail();
+  if (launch_leaf(la, c->num_sms, st, &launches, c->side_stream, c->fork_ev, c->join_ev)) return cuda_fail();
   if (use_events) cudaEventRecord(c->ev[5], st);
   if (mask_h) cudaMemcpyAsync(mask_h, c->d_mask, n, cudaMemcpyDeviceToHost, st);
   if (score_h) cudaMemcpyAsync(score_h, c->d_score, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st);
@@ -530,6 +536,12 @@ int denoise_create(denoise_ctx **out, int device, size_t max_points, uint32_t ma
       free_ctx(c);
       return DENOISE_E_CUDA;
     }
+  }
+  if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    free_ctx(c);
+    return DENOISE_E_CUDA;
   }
   *out = c;
   return DENOISE_OK;

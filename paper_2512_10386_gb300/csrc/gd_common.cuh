@@ -83,6 +83,8 @@ struct Counters {
   uint32_t n_leaves;
   uint32_t leaf_work;                    // persistent leaf-kernel work counter
   uint32_t leaf_work2;                   // the same for a second leaf-kernel pass (cross-leaf mode)
+  uint32_t leaf_work3;                   // the same for the launch that takes the small leaves
+  uint32_t split_leaf;                   // first index of the largest-first order with leaves of <= 128 points
   uint32_t xleaf_work;                   // cross-leaf kNN work counter
   uint32_t tile_work[kMaxPasses];        // radix-pass tile counters
   uint32_t cls_count[kLeafClasses];      // leaves per size class
@@ -196,6 +198,7 @@ struct LeafArgs {
   uint32_t ctas_per_sm;         // 0 = occupancy limit
   uint32_t threads;             // threads per leaf CTA: 64 or 128 (0 = 128)
   uint32_t spin_limit;          // iterations of the bounded bulk-copy wait (0 = kSpinLimit)
+  uint32_t part;                // leaves taken from the order: 0 all, 1 those before split_leaf, 2 the rest
   // cross-leaf kNN (denoise_params.cross_leaf): phase 1 runs the voxel gate only and
   // marks P_1; phase 3 runs the per-leaf steps after the kNN on the cross-leaf results
   uint32_t xphase;              // 0 (the fused method), 1 or 3
@@ -232,7 +235,11 @@ uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit);
 // Eq. 10-11 per leaf (box origin lo and voxel size h into the leaf table) and the
 // largest-first leaf order; must precede launch_leaf on the same stream.
 int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches);
-int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches);
+// With a side stream (and two events), the leaves of more than 128 points run on
+// `st` and the smaller ones concurrently on `side` (64-thread CTAs of a 128-point
+// layout), joined back into `st`; without, one launch takes every leaf.
+int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches, cudaStream_t side = nullptr,
+                cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 // the recording instantiation (debug / training outputs), in its own translation unit
 int launch_leaf_rec(const LeafArgs &a, int num_sms, cudaStream_t st);
 int launch_leaf_xl(const LeafArgs &a, int num_sms, cudaStream_t st);

@@ -27,6 +27,8 @@ __global__ void k_init(FrameInfo *frames, uint32_t nframes, Counters *ctr, uint3
     ctr->n_leaves = 0;
     ctr->leaf_work = 0;
     ctr->leaf_work2 = 0;
+    ctr->leaf_work3 = 0;
+    ctr->split_leaf = 0;
     ctr->xleaf_work = 0;
     for (int i = 0; i < kMaxPasses; ++i) ctr->tile_work[i] = 0;
     for (int i = 0; i < kLeafClasses; ++i) ctr->cls_count[i] = ctr->cls_cursor[i] = 0;

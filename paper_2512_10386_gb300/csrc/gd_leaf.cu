@@ -129,6 +129,8 @@ __global__ void __launch_bounds__(256) k_leaf_order(const Leaf *__restrict__ lea
       s_base[c] = run;
       run += ctr->cls_count[c];
     }
+    // the two smallest classes (1-64 and 65-128 points) come last
+    if (blockIdx.x == 0) ctr->split_leaf = s_base[kLeafClasses - 2];
   }
   __syncthreads();
   for (uint32_t b = blockIdx.x * blockDim.x; b < nl; b += gridDim.x * blockDim.x) {
@@ -190,10 +192,35 @@ int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launc
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches) {
-  if (launches) ++*launches;
-  if (a.xphase != 0) return launch_leaf_xl(a, num_sms, st);  // the cross-leaf phases: their own instantiation
-  return (a.use_dbg || a.use_train) ? launch_leaf_rec(a, num_sms, st) : launch_kmax<false, false>(a, num_sms, st);
+int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches, cudaStream_t side, cudaEvent_t fork,
+                cudaEvent_t join) {
+  if (a.xphase != 0) {  // the cross-leaf phases: their own instantiation
+    if (launches) ++*launches;
+    return launch_leaf_xl(a, num_sms, st);
+  }
+  auto go = [&](const LeafArgs &x, cudaStream_t s) {
+    return (x.use_dbg || x.use_train) ? launch_leaf_rec(x, num_sms, s) : launch_kmax<false, false>(x, num_sms, s);
+  };
+  // A small leaf's per-leaf steps keep few warps busy; on 64-thread CTAs of a
+  // 128-point shared-memory layout twice as many CTAs share an SM.  The large
+  // leaves keep their 128-thread CTAs; the two launches run side by side, and the
+  // small-leaf CTAs take the SMs the large-leaf CTAs leave (the order of the
+  // leaves and every result are the same as with one launch).
+  const bool split = side && fork && join && a.threads != 64 && a.lmax > 128 && a.ctas_per_sm == 0;
+  if (!split) {
+    if (launches) ++*launches;
+    return go(a, st);
+  }
+  LeafArgs big = a, small = a;
+  big.part = 1;
+  small.part = 2;
+  small.threads = 64;
+  small.lmax = 128;
+  if (launches) *launches += 2;
+  if (cudaEventRecord(fork, st) != cudaSuccess || cudaStreamWaitEvent(side, fork, 0) != cudaSuccess) return -1;
+  if (go(big, st) || go(small, side)) return -1;
+  if (cudaEventRecord(join, side) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess) return -1;
+  return 0;
 }
 
 }  // namespace gd

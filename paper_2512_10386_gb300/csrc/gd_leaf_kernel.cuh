@@ -1300,16 +1300,19 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : GD_LEAF_MIN_C
   }
   __syncthreads();
   pdl_wait();
-  const uint32_t n_leaves = A.ctr->n_leaves;
+  // the part of the largest-first order this launch takes: every leaf, or those
+  // before the split (more than 128 points), or from it (the small leaves)
+  const uint32_t n_all = A.ctr->n_leaves, split = A.ctr->split_leaf;
+  const uint32_t w_lo = (A.part == 2) ? split : 0u, w_hi = (A.part == 1) ? split : n_all;
+  uint32_t *const wctr = (kXl && A.xphase == 3) ? &A.ctr->leaf_work2
+                         : (A.part == 2)         ? &A.ctr->leaf_work3
+                                                 : &A.ctr->leaf_work;
   uint32_t phase = 0;
   for (;;) {
-    if (tid == 0)
-      S.leaf = (ld_volatile(&A.ctr->status) & kStFatal)
-                   ? 0xFFFFFFFFu
-                   : atomicAdd((kXl && A.xphase == 3) ? &A.ctr->leaf_work2 : &A.ctr->leaf_work, 1u);
+    if (tid == 0) S.leaf = (ld_volatile(&A.ctr->status) & kStFatal) ? 0xFFFFFFFFu : w_lo + atomicAdd(wctr, 1u);
     __syncthreads();
     const uint32_t wi = S.leaf;  // block-uniform: one thread decided
-    if (wi >= n_leaves) break;
+    if (wi >= w_hi) break;
     const Leaf lf = A.leaves[A.order[wi]];
     if (lf.count <= lmax) {
       if (tid == 0) {
