@@ -384,7 +384,8 @@ def run_ours(args):
     achieved = stats["knn_pairs"] * FLOP_PER_PAIR / (leaf_avg_ms / 1000.0) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak_tflops, "traffic": _profile_traffic(),
-                "kernel": "gd::k_leaf<32> (voxel gate + kNN + density gate + score + selection)",
+                "kernel": "gd::k_leaf<32> (voxel gate + kNN + density gate + score + selection; leaves of more "
+                          "and of at most 64 points in two concurrent launches, timed together)",
                 "work": f"{stats['knn_pairs']} candidate pairs x {FLOP_PER_PAIR:g} FP32 flop per launch",
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:g} MHz "
                               f"(max SM clock, {peak_kind} peaks file)",

@@ -55,6 +55,9 @@ struct Leaf {
 // leaves above the shared-memory size (global-memory path), then classes of 64
 // points from the largest down.
 constexpr int kLeafClasses = 9;
+// leaves of at most kSmallLeaf points run in their own launch (64-thread CTAs);
+// one 64-point size class (measured against 128 and 256: fastest)
+constexpr uint32_t kSmallLeaf = 64;
 
 // Programmatic dependent launch: every kernel of a call is launched so that its
 // blocks may be scheduled while the previous kernel drains; pdl_wait() (first
@@ -84,7 +87,7 @@ struct Counters {
   uint32_t leaf_work;                    // persistent leaf-kernel work counter
   uint32_t leaf_work2;                   // the same for a second leaf-kernel pass (cross-leaf mode)
   uint32_t leaf_work3;                   // the same for the launch that takes the small leaves
-  uint32_t split_leaf;                   // first index of the largest-first order with leaves of <= 128 points
+  uint32_t split_leaf;                   // first index of the largest-first order with leaves of <= kSmallLeaf points
   uint32_t xleaf_work;                   // cross-leaf kNN work counter
   uint32_t tile_work[kMaxPasses];        // radix-pass tile counters
   uint32_t cls_count[kLeafClasses];      // leaves per size class
@@ -235,9 +238,9 @@ uint32_t leaf_pick_lmax(uint32_t leaf_capacity, int kmax, size_t smem_limit);
 // Eq. 10-11 per leaf (box origin lo and voxel size h into the leaf table) and the
 // largest-first leaf order; must precede launch_leaf on the same stream.
 int launch_leaf_prep(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches);
-// With a side stream (and two events), the leaves of more than 128 points run on
-// `st` and the smaller ones concurrently on `side` (64-thread CTAs of a 128-point
-// layout), joined back into `st`; without, one launch takes every leaf.
+// With a side stream (and two events), the leaves of more than kSmallLeaf points
+// run on `st` and the smaller ones concurrently on `side` (64-thread CTAs of a
+// kSmallLeaf-point layout), joined back into `st`; without, one launch takes every leaf.
 int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches, cudaStream_t side = nullptr,
                 cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 // the recording instantiation (debug / training outputs), in its own translation unit

@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(256) k_leaf_order(const Leaf *__restrict__ lea
       s_base[c] = run;
       run += ctr->cls_count[c];
     }
-    // the two smallest classes (1-64 and 65-128 points) come last
-    if (blockIdx.x == 0) ctr->split_leaf = s_base[kLeafClasses - 2];
+    // the smallest classes (64 points each, up to kSmallLeaf points) come last
+    if (blockIdx.x == 0) ctr->split_leaf = s_base[kLeafClasses - (int)(kSmallLeaf / 64)];
   }
   __syncthreads();
   for (uint32_t b = blockIdx.x * blockDim.x; b < nl; b += gridDim.x * blockDim.x) {
@@ -202,11 +202,11 @@ int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches, 
     return (x.use_dbg || x.use_train) ? launch_leaf_rec(x, num_sms, s) : launch_kmax<false, false>(x, num_sms, s);
   };
   // A small leaf's per-leaf steps keep few warps busy; on 64-thread CTAs of a
-  // 128-point shared-memory layout twice as many CTAs share an SM.  The large
+  // 64-point shared-memory layout twice as many CTAs share an SM.  The large
   // leaves keep their 128-thread CTAs; the two launches run side by side, and the
   // small-leaf CTAs take the SMs the large-leaf CTAs leave (the order of the
   // leaves and every result are the same as with one launch).
-  const bool split = side && fork && join && a.threads != 64 && a.lmax > 128 && a.ctas_per_sm == 0;
+  const bool split = side && fork && join && a.threads != 64 && a.lmax > kSmallLeaf && a.ctas_per_sm == 0;
   if (!split) {
     if (launches) ++*launches;
     return go(a, st);
@@ -215,7 +215,7 @@ int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches, 
   big.part = 1;
   small.part = 2;
   small.threads = 64;
-  small.lmax = 128;
+  small.lmax = kSmallLeaf;
   if (launches) *launches += 2;
   if (cudaEventRecord(fork, st) != cudaSuccess || cudaStreamWaitEvent(side, fork, 0) != cudaSuccess) return -1;
   if (go(big, st) || go(small, side)) return -1;
