@@ -1301,7 +1301,7 @@ __global__ void __launch_bounds__(kLeafThreads, (KMAX >= 64) ? 1 : GD_LEAF_MIN_C
   __syncthreads();
   pdl_wait();
   // the part of the largest-first order this launch takes: every leaf, or those
-  // before the split (more than 128 points), or from it (the small leaves)
+  // before the split (more than kSmallLeaf points), or from it (the small leaves)
   const uint32_t n_all = A.ctr->n_leaves, split = A.ctr->split_leaf;
   const uint32_t w_lo = (A.part == 2) ? split : 0u, w_hi = (A.part == 1) ? split : n_all;
   uint32_t *const wctr = (kXl && A.xphase == 3) ? &A.ctr->leaf_work2
