@@ -214,7 +214,7 @@ int launch_leaf(const LeafArgs &a, int num_sms, cudaStream_t st, int *launches, 
   LeafArgs big = a, small = a;
   big.part = 1;
   small.part = 2;
-  small.threads = 64;
+  small.threads = 64;  // (32-thread CTAs: dense scan +1.7 %, 64 LiDAR frames -1.4 %)
   small.lmax = kSmallLeaf;
   if (launches) *launches += 2;
   if (cudaEventRecord(fork, st) != cudaSuccess || cudaStreamWaitEvent(side, fork, 0) != cudaSuccess) return -1;
