@@ -19,7 +19,9 @@ result is in host memory.
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import dataclasses
+import os
 import statistics
 import time
 from typing import Callable, Dict, Iterable, List, Optional, Sequence
@@ -54,10 +56,35 @@ class Completion:
         return self.t_done - self.t_arrival
 
 
+_STAGE_CHUNK_ROWS = 1 << 16   # rows (768 KB of xyz) per piece of a parallel staging copy
+
+
+def _stage_pieces(pieces, pool, threads: int) -> None:
+    """Copy (dst, src) array pairs; pieces above _STAGE_CHUNK_ROWS rows are split
+    into at most `threads` row ranges spread over `pool` (numpy releases the GIL
+    for a plain copy of one dtype, so the threads copy in parallel).  A dense
+    frame of ~1 M points is ~13 MB: on one thread the copy alone takes about as
+    long as the frame's device work, and it runs on the server's only control
+    thread."""
+    jobs = []
+    for dst, src in pieces:
+        n = len(src)
+        if pool is None or n <= _STAGE_CHUNK_ROWS:
+            np.copyto(dst, src)
+            continue
+        nch = min(threads, -(-n // _STAGE_CHUNK_ROWS))
+        step = -(-n // nch)
+        for a in range(0, n, step):
+            b = min(n, a + step)
+            jobs.append(pool.submit(np.copyto, dst[a:b], src[a:b]))
+    for j in jobs:
+        j.result()
+
+
 class _Slot:
     """One execution slot: a native context, a stream, pinned staging."""
 
-    def __init__(self, index: int, capacity: int, max_frames: int, params, device=None):
+    def __init__(self, index: int, capacity: int, max_frames: int, params, device=None, pool=None, threads: int = 1):
         import torch
 
         from .api import Denoiser
@@ -76,14 +103,17 @@ class _Slot:
         self.batch: Optional[List[Request]] = None
         self.offsets: List[int] = []
         self.t_admit = 0.0
+        self.pool, self.threads = pool, threads
 
     def launch(self, batch: List[Request], t_admit: float):
         offs = [0]
         xv = self.xyz.numpy()
+        pieces = []
         for r in batch:
             n = len(r.xyz)
-            xv[offs[-1]:offs[-1] + n] = r.xyz
+            pieces.append((xv[offs[-1]:offs[-1] + n], np.asarray(r.xyz, dtype=np.float32).reshape(n, 3)))
             offs.append(offs[-1] + n)
+        _stage_pieces(pieces, self.pool, self.threads)
         total = offs[-1]
         self.den.run_batch(self.xyz[:total], offs, self.params, mask=self.mask[:total], score=self.score[:total],
                            stage=self.stage[:total], stream=self.stream)
@@ -99,10 +129,14 @@ class _Slot:
         if st != N.DENOISE_OK:
             raise N.DenoiseError(st, "serving batch")
         out = []
+        if keep_results:  # the batch's results out of the pinned buffers, in one parallel copy
+            total = self.offsets[-1]
+            m, sc, sg = np.empty(total, np.uint8), np.empty(total, np.float32), np.empty(total, np.uint8)
+            _stage_pieces([(m, self.mask[:total].numpy()), (sc, self.score[:total].numpy()),
+                           (sg, self.stage[:total].numpy())], self.pool, self.threads)
         for i, r in enumerate(self.batch):
             a, b = self.offsets[i], self.offsets[i + 1]
-            res = ((self.mask[a:b].numpy().copy(), self.score[a:b].numpy().copy(), self.stage[a:b].numpy().copy())
-                   if keep_results else (None, None, None))
+            res = (m[a:b], sc[a:b], sg[a:b]) if keep_results else (None, None, None)
             out.append(Completion(r.rid, r.kind, b - a, r.t_arrival, self.t_admit, t_done, self.index,
                                   len(self.batch), *res))
         self.batch = None
@@ -156,14 +190,24 @@ class Server:
     """Continuous-batching denoising server on one GPU."""
 
     def __init__(self, params, capacities: Sequence[int], max_frames: int = 8,
-                 budget_points: Optional[int] = None, device=None):
+                 budget_points: Optional[int] = None, device=None, copy_threads: Optional[int] = None):
+        """copy_threads: host threads for staging request points into the slots'
+        pinned buffers (default: half the host cores, at most 8; 0 or 1 = copy
+        on the calling thread)."""
         self.params = params
-        self.slots = [_Slot(i, c, max_frames, params, device) for i, c in enumerate(capacities)]
+        if copy_threads is None:
+            copy_threads = max(1, min(8, (os.cpu_count() or 2) // 2))
+        self.pool = concurrent.futures.ThreadPoolExecutor(copy_threads) if copy_threads > 1 else None
+        self.slots = [_Slot(i, c, max_frames, params, device, self.pool, copy_threads)
+                      for i, c in enumerate(capacities)]
         self.sched = Scheduler(capacities, max_frames, budget_points or sum(capacities))
 
     def close(self):
         for s in self.slots:
             s.close()
+        if self.pool is not None:
+            self.pool.shutdown()
+            self.pool = None
 
     def serve(self, requests: Iterable[Request], realtime: bool = True, clock: Callable[[], float] = time.perf_counter,
               idle_sleep: float = 2e-4, keep_results: bool = True) -> List[Completion]:

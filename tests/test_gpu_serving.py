@@ -2,8 +2,9 @@
 
 A compressed Poisson stream of mixed-size frames is played through the
 continuous-batching server (several slots, multi-frame batches, overlapping
-work); each completion must equal the frame's solo denoise_run result bit for
-bit, and the test checks that batches did overlap in time.
+work, frames large enough for the parallel staging copy); each completion must
+equal the frame's solo denoise_run result bit for bit, and the test checks that
+batches did overlap in time.
 """
 
 import numpy as np
@@ -30,6 +31,11 @@ def test_results_identical_alone_and_in_the_mix():
         n_surface = int(rng.choice([2000, 6000, 15000, 40000]))
         xyz, _ = synth.object_cloud(seed=200 + i, n_surface=n_surface)
         reqs.append(Request(i, t, xyz, kind=str(n_surface)))
+    # two frames above the staging copy's chunk size (their points and results move in row ranges on the copy threads)
+    for i in (16, 17):
+        t += rng.exponential(1 / 400.0)
+        xyz, _ = synth.object_cloud(seed=200 + i, n_surface=90000)
+        reqs.append(Request(i, t, xyz, kind="90000"))
     P = Params(k=16)
     srv = Server(P, capacities=[50_000, 50_000, 120_000], max_frames=4)
     try:
@@ -39,8 +45,8 @@ def test_results_identical_alone_and_in_the_mix():
         rep = latency_report(comps, time.perf_counter() - t0)
     finally:
         srv.close()
-    assert [c.rid for c in comps] == list(range(16))
-    d = Denoiser(max_points=60_000)
+    assert [c.rid for c in comps] == list(range(18))
+    d = Denoiser(max_points=120_000)
     try:
         for c, r in zip(comps, reqs):
             solo = d.run(torch.from_numpy(r.xyz).cuda(), P)

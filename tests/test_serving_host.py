@@ -47,3 +47,25 @@ def test_latency_report_percentiles():
     assert rep["frames"] == 100 and rep["points"] == 1000
     assert rep["latency_ms_p50"] == pytest.approx(51.0) or rep["latency_ms_p50"] == pytest.approx(50.0)
     assert rep["latency_ms_p99"] == pytest.approx(99.0, abs=1.0)
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_parallel_staging_copy_places_every_row(threads):
+    """The slots' staging copy: frames of a batch land back to back, large ones
+    split into row ranges over the copy threads, small ones copied whole."""
+    import concurrent.futures
+
+    from paper_2512_10386_gb300.serving import _STAGE_CHUNK_ROWS, _stage_pieces
+    rng = np.random.default_rng(3)
+    sizes = [5, _STAGE_CHUNK_ROWS, _STAGE_CHUNK_ROWS + 1, 3 * _STAGE_CHUNK_ROWS + 17, 0]
+    frames = [rng.standard_normal((n, 3)).astype(np.float32) for n in sizes]
+    dst = np.full((sum(sizes) + 4, 3), np.nan, dtype=np.float32)
+    offs = np.cumsum([0] + sizes)
+    pool = concurrent.futures.ThreadPoolExecutor(threads) if threads > 1 else None
+    try:
+        _stage_pieces([(dst[offs[i]:offs[i + 1]], f) for i, f in enumerate(frames)], pool, threads)
+    finally:
+        if pool is not None:
+            pool.shutdown()
+    assert np.array_equal(dst[:offs[-1]], np.concatenate(frames))
+    assert np.isnan(dst[offs[-1]:]).all()              # nothing written past the batch
