@@ -18,9 +18,10 @@
  *    (cudaPointerGetAttributes).  Host buffers are staged through the
  *    context's device memory, in stream order on the given stream: pinned
  *    (page-locked, mapped) host input is read in place by the first kernel,
- *    which writes the device copy; other host input is copied first; host
- *    outputs are copied back at the end of the call.  Pinned host memory
- *    keeps all of it asynchronous.
+ *    which writes the device copy; other host input is copied first.  Host
+ *    outputs are filled at the end of the call: pinned ones by a kernel that
+ *    stores through their mapped addresses (any byte offset), others by the
+ *    copy engine.  Pinned host memory keeps all of it asynchronous.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  All work
  *    of a call is ordered on that stream.
  *  - The caller owns every buffer it passes; the context owns all scratch.

@@ -58,6 +58,7 @@ struct denoise_ctx {
   bool staged_rec[kSlots] = {};
   int slot = 0;
   Counters *h_ctr = nullptr;
+  Counters *h_ctr_dev = nullptr;  // mapped device address of h_ctr (null: copied by the copy engine)
   double *h_grad = nullptr;
   // options
   int sync = 1, graphs = 0, profiling = 0, training = 0;
@@ -86,6 +87,8 @@ struct denoise_ctx {
   // frame layout cache
   std::vector<uint64_t> layout;
   uint32_t ntiles = 0;
+  uint64_t layout_gen = 0;        // bumped at every layout change
+  uint64_t tables_gen = ~0ull;    // layout generation that d_tiles / d_frames hold (after a direct call)
 };
 
 namespace {
@@ -97,14 +100,17 @@ constexpr size_t kBackPartials = 1024;
 // the kernels could not read without peer access).
 enum class Loc { kHost, kDevice, kOtherDevice };
 
-Loc locate(const void *p, int device) {
+// For pinned host memory `mapped` (if given) receives its device address, else null.
+Loc locate(const void *p, int device, void **mapped = nullptr) {
   cudaPointerAttributes at;
+  if (mapped) *mapped = nullptr;
   if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return Loc::kHost;
   }
   if (at.type == cudaMemoryTypeManaged) return Loc::kDevice;
   if (at.type == cudaMemoryTypeDevice) return at.device == device ? Loc::kDevice : Loc::kOtherDevice;
+  if (mapped && at.type == cudaMemoryTypeHost) *mapped = at.devicePointer;
   return Loc::kHost;
 }
 
@@ -207,7 +213,8 @@ uint32_t build_tiles(denoise_ctx *c, const uint64_t *offsets, uint32_t nframes) 
 // Enqueue one whole call on `st`.  Returns a DENOISE status (host-side errors only).
 int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, const denoise_params &p,
             uint8_t *mask, float *score, uint8_t *stage, const denoise_debug *dbg, bool use_events,
-            cudaStream_t st, const float *xyz_host, uint8_t *mask_h, float *score_h, uint8_t *stage_h) {
+            cudaStream_t st, const float *xyz_host, uint8_t *mask_h, float *score_h, uint8_t *stage_h,
+            void *const out_mapped[3]) {
   int launches = 0;
   // Pinned host input is read in place by the bounding-box pass, which writes the
   // device copy on the way (one pass over the link, overlapped with the reduction);
@@ -218,8 +225,17 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
         cudaSuccess)
       return cuda_fail();
   }
-  cudaMemcpyAsync(c->d_tiles, c->h_tiles[c->slot], sizeof(Tile) * c->ntiles, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(c->d_frames, c->h_frames[c->slot], sizeof(FrameInfo) * nframes, cudaMemcpyHostToDevice, st);
+  // The tile and frame tables go up when the layout changed since the last direct
+  // call that uploaded them (no kernel writes a tile or a frame's bounds; a frame's
+  // per-call fields are reset on the device), and always into a captured graph,
+  // which has to stand alone.
+  const bool capturing = st == c->cap_stream;
+  const bool upload = capturing || c->tables_gen != c->layout_gen;
+  if (upload) {
+    if (!capturing) c->tables_gen = ~0ull;  // valid again only once this call is enqueued
+    cudaMemcpyAsync(c->d_tiles, c->h_tiles[c->slot], sizeof(Tile) * c->ntiles, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d_frames, c->h_frames[c->slot], sizeof(FrameInfo) * nframes, cudaMemcpyHostToDevice, st);
+  }
   if (use_events) cudaEventRecord(c->ev[0], st);
   FrontArgs fa{};
   fa.xyz = xyz_dev;
@@ -313,12 +329,27 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
   }
   if (launch_leaf(la, c->num_sms, st, &launches, c->side_stream, c->fork_ev, c->join_ev)) return cuda_fail();
   if (use_events) cudaEventRecord(c->ev[5], st);
-  if (mask_h) cudaMemcpyAsync(mask_h, c->d_mask, n, cudaMemcpyDeviceToHost, st);
-  if (score_h) cudaMemcpyAsync(score_h, c->d_score, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st);
-  if (stage_h) cudaMemcpyAsync(stage_h, c->d_stage, n, cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+  // Results into host buffers: pinned ones and the counters by one kernel through
+  // their mapped addresses; other host memory (and everything, where the counters
+  // have no mapped address) by the copy engine.
+  const bool by_sms = c->h_ctr_dev != nullptr;
+  uint8_t *mask_m = by_sms && mask_h ? static_cast<uint8_t *>(out_mapped[0]) : nullptr;
+  float *score_m = by_sms && score_h ? static_cast<float *>(out_mapped[1]) : nullptr;
+  uint8_t *stage_m = by_sms && stage_h ? static_cast<uint8_t *>(out_mapped[2]) : nullptr;
+  if (mask_h && !mask_m) cudaMemcpyAsync(mask_h, c->d_mask, n, cudaMemcpyDeviceToHost, st);
+  if (score_h && !score_m) cudaMemcpyAsync(score_h, c->d_score, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (stage_h && !stage_m) cudaMemcpyAsync(stage_h, c->d_stage, n, cudaMemcpyDeviceToHost, st);
+  if (by_sms) {
+    const OutArgs oa{c->d_mask, c->d_score, c->d_stage, mask_m, score_m, stage_m, n, c->d_ctr, c->h_ctr_dev};
+    if (launch_out(oa, c->num_sms, st)) return cuda_fail();
+    ++launches;
+  } else {
+    cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+  }
   c->last_launches = launches;
-  return cudaGetLastError() == cudaSuccess ? DENOISE_OK : DENOISE_E_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return DENOISE_E_CUDA;
+  if (upload && !capturing) c->tables_gen = c->layout_gen;
+  return DENOISE_OK;
 }
 
 int finish(denoise_ctx *c, cudaStream_t st, bool events) {
@@ -362,9 +393,10 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
 
   // resolve host / device buffers (device memory of another GPU is rejected)
   const Loc lx = locate(xyz, c->device);
-  const Loc lm = mask ? locate(mask, c->device) : Loc::kDevice;
-  const Loc ls = score ? locate(score, c->device) : Loc::kDevice;
-  const Loc lg = stage ? locate(stage, c->device) : Loc::kDevice;
+  void *out_mapped[3] = {nullptr, nullptr, nullptr};  // device addresses of pinned host outputs
+  const Loc lm = mask ? locate(mask, c->device, &out_mapped[0]) : Loc::kDevice;
+  const Loc ls = score ? locate(score, c->device, &out_mapped[1]) : Loc::kDevice;
+  const Loc lg = stage ? locate(stage, c->device, &out_mapped[2]) : Loc::kDevice;
   if (lx == Loc::kOtherDevice || lm == Loc::kOtherDevice || ls == Loc::kOtherDevice || lg == Loc::kOtherDevice)
     return DENOISE_E_INVAL;
   const bool xyz_dev = lx == Loc::kDevice;
@@ -387,6 +419,7 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
     c->slot = ns;
     c->layout.assign(offsets, offsets + nframes + 1);
     c->ntiles = build_tiles(c, offsets, nframes);
+    ++c->layout_gen;
   }
   const bool events = c->profiling && !c->graphs && c->sync;
   int rc;
@@ -409,6 +442,7 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
     put(&c->wait_limit, sizeof(c->wait_limit));
     put(&c->hold_tile1, sizeof(c->hold_tile1));
     put(offsets, sizeof(uint64_t) * (nframes + 1));
+    put(&c->slot, sizeof(c->slot));  // the staging slot the graph's table copies read (rewritten for other layouts)
     if (!c->gexec || key != c->gkey) {
       if (c->gexec) {
         cudaStreamSynchronize(st);
@@ -420,7 +454,7 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
       cudaGraph_t g = nullptr;
       if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_fail();
       rc = enqueue(c, xyz_d, n, nframes, *p, mask_d, score_d, stage_d, nullptr, false, c->cap_stream, xyz_h, mask_h,
-                   score_h, stage_h);
+                   score_h, stage_h, out_mapped);
       const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
       if (rc || ce != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -438,7 +472,7 @@ int run_impl(denoise_ctx *c, const float *xyz, const uint64_t *offsets, uint32_t
     if (cudaGraphLaunch(c->gexec, st) != cudaSuccess) return cuda_fail();
   } else {
     rc = enqueue(c, xyz_d, n, nframes, *p, mask_d, score_d, stage_d, dbg, events, st, xyz_h, mask_h, score_h,
-                 stage_h);
+                 stage_h, out_mapped);
     if (rc) return rc;
   }
   if (cudaEventRecord(c->staged[c->slot], st) != cudaSuccess) return cuda_fail();
@@ -525,6 +559,10 @@ int denoise_create(denoise_ctx **out, int device, size_t max_points, uint32_t ma
     return DENOISE_E_NOMEM;
   }
   memset(c->h_ctr, 0, sizeof(Counters));
+  if (cudaHostGetDevicePointer((void **)&c->h_ctr_dev, c->h_ctr, 0) != cudaSuccess) {
+    cudaGetLastError();
+    c->h_ctr_dev = nullptr;
+  }
   for (auto &ev : c->ev) {
     if (cudaEventCreate(&ev) != cudaSuccess) {
       free_ctx(c);

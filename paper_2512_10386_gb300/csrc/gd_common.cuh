@@ -15,6 +15,7 @@ constexpr int kFrontThreads = 256;
 constexpr int kFrontItems = kTilePts / kFrontThreads; // 8
 static_assert(kFrontThreads == 256, "the radix pass maps one thread to each 8-bit digit");
 static_assert(kTilePts % kFrontThreads == 0, "whole items per thread");
+static_assert(kTilePts % (4 * kFrontThreads) == 0, "whole 4-point groups per thread (bounding-box pass)");
 constexpr int kMaxPasses = 8;                         // 8-bit radix digits over <= 63 key bits
 // The radix sort runs over the top key bits only (at most kTopPasses digits: the
 // octree down to some level DB); below DB the full order is only needed inside the
@@ -283,5 +284,19 @@ struct BackArgs {
 };
 int launch_soft_removal(const BackArgs &a, cudaStream_t st);
 int launch_backward(const BackArgs &a, cudaStream_t st, int *launches);
+
+// Results into pinned host memory (mapped device addresses; a null destination is skipped).
+struct OutArgs {
+  const uint8_t *mask_d;
+  const float *score_d;
+  const uint8_t *stage_d;
+  uint8_t *mask_h;
+  float *score_h;
+  uint8_t *stage_h;
+  uint32_t n;
+  const Counters *ctr_d;
+  Counters *ctr_h;
+};
+int launch_out(const OutArgs &a, int num_sms, cudaStream_t st);
 
 }  // namespace gd

@@ -61,21 +61,64 @@ __global__ void __launch_bounds__(kFrontThreads) k_bbox(const float *__restrict_
   const Tile t = tiles[blockIdx.x];
   uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, mx[3] = {0u, 0u, 0u};
   bool bad = false;
-  // a tile holds at most kFrontItems points per thread: unrolled, so that all
-  // loads are in flight at once
+  auto take = [&](int a, float v) {
+    bad |= !isfinite(v);
+    const uint32_t o = f2ord(v);
+    mn[a] = min(mn[a], o);
+    mx[a] = max(mx[a], o);
+  };
+  auto point = [&](uint32_t i) {  // one point, scalar loads (and the device copy of host input)
 #pragma unroll
-  for (int it = 0; it < kFrontItems; ++it) {
-    const uint32_t i = t.begin + it * kFrontThreads + threadIdx.x;
-    if (i < t.end) {
+    for (int a = 0; a < 3; ++a) {
+      const float v = xyz[3ull * i + a];
+      if (xyz_copy) xyz_copy[3ull * i + a] = v;
+      take(a, v);
+    }
+  };
+  const bool vec = ((reinterpret_cast<uintptr_t>(xyz) | reinterpret_cast<uintptr_t>(xyz_copy)) & 15u) == 0;
+  if (vec) {
+    // from the first point index that is a multiple of 4, groups of 4 points (3
+    // aligned 16-byte words) are read by consecutive threads -- every warp load
+    // covers 512 contiguous bytes, all of a thread's loads issued together (the
+    // input may be host memory, read across the link) -- and staged in shared
+    // memory; the few points before and after the groups are read one by one.
+    __shared__ float4 s_v[kTilePts / 4 * 3];
+    const uint32_t p0 = min(t.end, (t.begin + 3u) & ~3u);
+    const uint32_t ng = (t.end - p0) >> 2, p1 = p0 + 4u * ng, nv = 3u * ng;
+    const float4 *src = reinterpret_cast<const float4 *>(xyz) + 3ull * (p0 >> 2);
+    float4 *dst = xyz_copy ? reinterpret_cast<float4 *>(xyz_copy) + 3ull * (p0 >> 2) : nullptr;
+    constexpr int kV = kTilePts / 4 * 3 / kFrontThreads;  // words per thread
+    float4 v[kV];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float v = xyz[3ull * i + a];
-        if (xyz_copy) xyz_copy[3ull * i + a] = v;  // host input read in place: the device copy
-        bad |= !isfinite(v);
-        const uint32_t o = f2ord(v);
-        mn[a] = min(mn[a], o);
-        mx[a] = max(mx[a], o);
+    for (int it = 0; it < kV; ++it) {
+      const uint32_t q = it * kFrontThreads + threadIdx.x;
+      if (q < nv) v[it] = src[q];
+    }
+#pragma unroll
+    for (int it = 0; it < kV; ++it) {
+      const uint32_t q = it * kFrontThreads + threadIdx.x;
+      if (q < nv) {
+        s_v[q] = v[it];
+        if (dst) dst[q] = v[it];
       }
+    }
+    const uint32_t nh = p0 - t.begin;  // < 4
+    if (threadIdx.x < nh) point(t.begin + threadIdx.x);
+    else if (threadIdx.x >= 32u && threadIdx.x - 32u < t.end - p1) point(p1 + threadIdx.x - 32u);
+    __syncthreads();
+    const float *sf = reinterpret_cast<const float *>(s_v);
+    for (uint32_t i = threadIdx.x; i < 4u * ng; i += kFrontThreads) {
+      take(0, sf[3u * i]);
+      take(1, sf[3u * i + 1u]);
+      take(2, sf[3u * i + 2u]);
+    }
+  } else {
+    // a tile holds at most kFrontItems points per thread: unrolled, so that all
+    // loads are in flight at once
+#pragma unroll
+    for (int it = 0; it < kFrontItems; ++it) {
+      const uint32_t i = t.begin + it * kFrontThreads + threadIdx.x;
+      if (i < t.end) point(i);
     }
   }
   for (int a = 0; a < 3; ++a) {

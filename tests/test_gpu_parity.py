@@ -265,6 +265,56 @@ def test_pageable_host_input_matches_device_input(dn):
     assert torch.equal(rd.stage.cpu(), rp.stage.cpu())
 
 
+def test_host_outputs_any_alignment_and_pageable(dn):
+    """Results into pinned host buffers are written by one kernel through their
+    mapped addresses (16-byte stores where source and destination offsets agree,
+    bytes elsewhere); pageable ones go through the copy engine.  Every placement
+    gives the device results, and no byte outside a result buffer changes."""
+    import synth
+    xyz, _ = synth.object_cloud(seed=12, n_surface=7001)
+    n = xyz.shape[0]
+    P = P_(k=16)
+    rd = dn.run(torch.from_numpy(xyz).cuda(), P)
+    want = (rd.mask.cpu(), rd.score.cpu(), rd.stage.cpu())
+    xh = torch.from_numpy(xyz).pin_memory()
+    for off in (0, 1, 3, 16, 17):
+        bm = torch.full((n + 64,), 0xA5, dtype=torch.uint8).pin_memory()
+        bs = torch.full((n + 64,), -7.0, dtype=torch.float32).pin_memory()
+        bg = torch.full((n + 64,), 0x5A, dtype=torch.uint8).pin_memory()
+        r = dn.run(xh, P, mask=bm[off:off + n], score=bs[off:off + n], stage=bg[off:off + n])
+        for got, exp in zip((r.mask, r.score, r.stage), want):
+            assert torch.equal(got, exp), off
+        for b, fill in ((bm, 0xA5), (bs, -7.0), (bg, 0x5A)):
+            assert bool((b[:off] == fill).all()) and bool((b[off + n:] == fill).all()), off
+    # pageable outputs (copy engine), alone and mixed with pinned ones
+    pm, ps, pg = torch.empty(n, dtype=torch.uint8), torch.empty(n), torch.empty(n, dtype=torch.uint8)
+    assert not pm.is_pinned()
+    r = dn.run(xh, P, mask=pm, score=ps, stage=pg)
+    assert torch.equal(pm, want[0]) and torch.equal(ps, want[1]) and torch.equal(pg, want[2])
+    qm = torch.empty(n, dtype=torch.uint8).pin_memory()
+    ps2 = torch.empty(n)
+    r = dn.run(xh, P, mask=qm, score=ps2)
+    assert torch.equal(qm, want[0]) and torch.equal(ps2, want[1]) and torch.equal(r.stage.cpu(), want[2])
+
+
+def test_input_at_any_point_offset(dn):
+    """The bounding-box pass reads 16-byte words where the input (and its device
+    copy) allow and single values elsewhere: device and pinned host input that
+    start 1, 2 or 3 points into a buffer give the aligned input's results."""
+    import synth
+    xyz, _ = synth.object_cloud(seed=13, n_surface=9001)
+    n = xyz.shape[0]
+    P = P_(k=16)
+    rd = dn.run(torch.from_numpy(xyz).cuda(), P)
+    for off in (1, 2, 3):
+        buf = torch.zeros((n + 4, 3), dtype=torch.float32)
+        buf[off:off + n] = torch.from_numpy(xyz)
+        for src in (buf.cuda(), buf.pin_memory()):
+            r = dn.run(src[off:off + n], P)
+            assert torch.equal(r.mask.cpu(), rd.mask.cpu()) and torch.equal(r.score.cpu(), rd.score.cpu()), off
+            assert torch.equal(r.stage.cpu(), rd.stage.cpu()), off
+
+
 def test_deterministic_bytes(dn):
     import synth
     xyz, _ = synth.object_cloud(seed=10, n_surface=20000)
@@ -336,6 +386,38 @@ def test_graph_mode_matches_direct(dn):
         dn.set_graphs(False)
     ref2 = dn.run(t, P_(k=8))
     assert torch.equal(r2.mask, ref2.mask) and torch.equal(r2.score, ref2.score)
+
+
+def test_layout_changes_direct_and_graph(dn):
+    """The tile and frame tables are uploaded only when the frame layout changes
+    (repeated layouts reuse the device copy), and a captured graph is replayed
+    only while the staging slot its table copies read still holds its layout:
+    alternating sizes, repeats, and a graph replay after the staging ring has
+    wrapped through other layouts all give the direct results."""
+    import synth
+    xyz, _ = synth.object_cloud(seed=14, n_surface=12000)
+    t = torch.from_numpy(xyz).cuda()
+    sizes = [t.shape[0], 9000, 7001, 5003, 3000, 2001]
+    P = P_(k=16)
+    ref = {n: dn.run(t[:n], P) for n in sizes}
+    ref = {n: (r.mask.clone(), r.score.clone()) for n, r in ref.items()}
+
+    def same(n, r):
+        return torch.equal(r.mask, ref[n][0]) and torch.equal(r.score, ref[n][1])
+
+    for n in (sizes[1], sizes[1], sizes[2], sizes[1], sizes[1], sizes[0]):
+        assert same(n, dn.run(t[:n], P)), n
+    dn.set_graphs(True)
+    try:
+        assert same(sizes[0], dn.run(t[:sizes[0]], P))          # captured
+        dn.set_graphs(False)
+        for n in sizes[1:]:                                       # the ring of staging slots wraps
+            assert same(n, dn.run(t[:n], P)), n
+        dn.set_graphs(True)
+        for _ in range(2):
+            assert same(sizes[0], dn.run(t[:sizes[0]], P))      # re-captured, then replayed
+    finally:
+        dn.set_graphs(False)
 
 
 def test_errors(dn):
