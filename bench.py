@@ -348,23 +348,21 @@ def run_ours(args):
     from paper_2512_10386_gb300 import _native as N
     N.check(d.status(stream), "denoise_run")
     d.set_sync(True)
-    # per-kernel times of the same step (library events between its stages), outside the timed region
+    # per-kernel times of the same step (library events between its stages), outside the timed region,
+    # interleaved with the same cloud with the score stage switched off (A3: P_2 kept, no score, no
+    # selection): the difference of the two medians is the time of the score and selection phases
     d.set_profiling(True)
-    leaf_ms = []
+    P_noscore = Params(k=32, leaf_capacity=512, stage_off=4)
+    out_ns = d.run(xyz, P_noscore, stream=stream)
+    leaf_ms, leaf_ms_noscore = [], []
     for s in range(min(args.steps, 10)):
         with torch.cuda.stream(stream):
             flush.fill_(float(s))
         d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
         leaf_ms.append(d.stats()["stage_ms"][4])
-    stats = d.stats()
-    # the same cloud with the score stage switched off (A3: P_2 kept, no score, no
-    # selection): the difference is the time of the score and selection phases
-    P_noscore = Params(k=32, leaf_capacity=512, stage_off=4)
-    out_ns = d.run(xyz, P_noscore, stream=stream)
-    leaf_ms_noscore = []
-    for s in range(min(args.steps, 10)):
+        stats = d.stats()
         with torch.cuda.stream(stream):
-            flush.fill_(float(s))
+            flush.fill_(float(s) + 0.5)
         d.run(xyz, P_noscore, mask=out_ns.mask, score=out_ns.score, stage=out_ns.stage, stream=stream)
         leaf_ms_noscore.append(d.stats()["stage_ms"][4])
     d.set_profiling(False)
@@ -396,8 +394,8 @@ def run_ours(args):
     # fraction over the whole kernel's time is reported beside it
     xu_peak = props.multi_processor_count * XU_PER_SM_CLK * sm_mhz * 1e6 / 1e12
     xu_ops = stats["score_terms"] * XU_OPS_PER_TERM
-    noscore_ms = sum(leaf_ms_noscore) / len(leaf_ms_noscore)
-    score_phase_ms = leaf_avg_ms - noscore_ms
+    noscore_ms = float(np.median(leaf_ms_noscore))
+    score_phase_ms = float(np.median(leaf_ms)) - noscore_ms
     # (a difference lost in the timing noise -- as under a profiler -- gives no figure)
     xu_achieved = xu_ops / (score_phase_ms / 1000.0) / 1e12 if score_phase_ms > 0.02 * leaf_avg_ms else None
     roofline_score = {"bound": "xu", "achieved": xu_achieved, "peak": xu_peak, "unit": "Tops/s",
