@@ -355,7 +355,7 @@ def run_ours(args):
     P_noscore = Params(k=32, leaf_capacity=512, stage_off=4)
     out_ns = d.run(xyz, P_noscore, stream=stream)
     leaf_ms, leaf_ms_noscore = [], []
-    for s in range(min(args.steps, 10)):
+    for s in range(max(1, min(args.steps, 10))):
         with torch.cuda.stream(stream):
             flush.fill_(float(s))
         d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
