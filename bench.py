@@ -22,7 +22,8 @@ Extra objects on the line:
                 cloud (gates identical, scores within 1e-5, masks identical
                 outside the tolerance band; counts of each)
   roofline_score the score phase's SFU (XU) work, ex2 + rcp per neighbour term,
-                against the SFU peak, over the whole leaf kernel's time
+                against the SFU peak, over the score phase's time (the leaf
+                stage with and without the score stage, interleaved medians)
   cpu_baseline  the FP64 oracle on the full cloud: single-threaded and with
                 the leaves spread over all host cores
   batched       64 LiDAR frames (60k-130k points) as one graph-captured batch,
@@ -31,6 +32,10 @@ Extra objects on the line:
                 continuous-batching server in real time (latency p50/p99),
                 the highest arrival rate whose p99 latency stays within one
                 20 Hz period, and frames all at once (throughput)
+  variants      the cross-leaf kNN, the ablation toggles (Table 9), the score on
+                a kNN within P_2, one leaf without the octree (Table 8), and the
+                evaluation calls (PSNR / Chamfer, Eq. 29-30; the Sec. 2.2
+                baseline), each timed with its candidate pairs and FP32 fraction
 ``--impl reference`` times the FP64 oracle instead (the reference arm).
 """
 
@@ -316,7 +321,7 @@ def run_ours(args):
         __graft_entry__.build()
     from paper_2512_10386_gb300 import Denoiser, Params
 
-    xyz_np, _ = _workload(rank)
+    xyz_np, labels_np = _workload(rank)
     n = len(xyz_np)
     P = Params(k=32, leaf_capacity=512)
     d = Denoiser(max_points=n, device=local)
@@ -456,6 +461,7 @@ def run_ours(args):
         d.run(xyz, P, mask=out.mask, score=out.score, stage=out.stage, stream=stream)
     torch.cuda.synchronize()
     clocks.__exit__(None, None, None)
+    out_mask_np = out.mask.cpu().numpy()
     d.close()
 
     batched = None
@@ -464,6 +470,12 @@ def run_ours(args):
     serving = None
     if args.serving_frames > 0 and rank == 0:
         serving = run_serving(args)
+    variants = None
+    if not args.no_variants and rank == 0:
+        try:
+            variants = run_variants(xyz_np, labels_np, out_mask_np, fp32_peak_tflops, stream)
+        except Exception as e:  # a failed variant call must not cost the headline line
+            variants = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     if rank != 0:
         if dist:
@@ -481,7 +493,7 @@ def run_ours(args):
         "ms_per_frame": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
         "roofline": roofline, "roofline_score": roofline_score, "parity": parity, "e2e": e2e, "cpu_baseline": cpu,
         "graph_replay": graph, "batched": batched,
-        "serving": serving,
+        "serving": serving, "variants": variants,
         "clocks": clocks.summary(), "gpu_launches": launches,
         "stats": {k: stats[k] for k in ("n_leaves", "knn_pairs", "n_p1", "n_p2", "score_terms", "launches")},
     }
@@ -489,6 +501,96 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def run_variants(xyz_np, labels_np, mask_np, fp32_peak_tflops, stream):
+    """The method's variants and the evaluation calls, each timed on its own
+    (CUDA events on the call's stream, median of a few calls after one untimed
+    call) with its candidate pairs and its FP32 fraction (8 flop a pair, as the
+    leaf kernel's roofline):
+      cross_leaf   kNN over the 27 same-level cells around each leaf, on the timed cloud
+      A1/A2/A3     one gate or the score selection switched off (Table 9), on the timed cloud
+      rescore_p2   the score on a kNN recomputed within P_2, on the timed cloud
+      octree_off   one leaf for the whole cloud (Table 8), on the 36,750-point object cloud
+                   (K = 16): the leaf is one CTA's work, so one SM of the GPU runs it
+      metrics      PSNR / Chamfer distance (Eq. 29-30) between the timed cloud's clean points
+                   and its denoised result (brute-force nearest neighbours both ways)
+      baseline     the gravitational-function method of Sec. 2.2 on the timed cloud
+                   (neighbour counts within R by brute force)"""
+    import torch
+
+    import synth
+    from paper_2512_10386_gb300 import Denoiser, Params
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.median(ms))
+
+    def entry(points, ms, pairs):
+        return {"points": int(points), "ms": ms, "points_per_s": points / (ms / 1000.0), "pairs": int(pairs),
+                "fp32_frac": pairs * FLOP_PER_PAIR / (ms / 1000.0) / 1e12 / fp32_peak_tflops}
+
+    n = len(xyz_np)
+    xyz = torch.from_numpy(xyz_np).cuda()
+    out = {"workload": WORKLOAD + " (octree off: the 36,750-point object cloud, K = 16)",
+           "timing": "CUDA events around each call (device buffers, one host synchronisation a call), median"}
+    d = Denoiser(max_points=n)
+    try:
+        base = Params(k=32, leaf_capacity=512)
+        for name, P in (("A1_voxel_gate_off", Params(k=32, leaf_capacity=512, stage_off=1)),
+                        ("A2_density_gate_off", Params(k=32, leaf_capacity=512, stage_off=2)),
+                        ("A3_score_selection_off", Params(k=32, leaf_capacity=512, stage_off=4)),
+                        ("rescore_p2", Params(k=32, leaf_capacity=512, rescore_p2=1))):
+            r = d.run(xyz, P, stream=stream)
+            ms = timed(lambda: d.run(xyz, P, mask=r.mask, score=r.score, stage=r.stage, stream=stream), 7)
+            out[name] = entry(n, ms, d.stats()["knn_pairs"])
+        ref = d.run(xyz, base, stream=stream).mask.clone()
+        d.set_cross_leaf(True)
+        Px = Params(k=32, leaf_capacity=512, cross_leaf=1)
+        r = d.run(xyz, Px, stream=stream)
+        ms = timed(lambda: d.run(xyz, Px, mask=r.mask, score=r.score, stage=r.stage, stream=stream), 5)
+        out["cross_leaf"] = entry(n, ms, d.stats()["knn_pairs"])
+        out["cross_leaf"]["mask_differs_from_leaf_local"] = float((r.mask != ref).float().mean().item())
+        d.set_cross_leaf(False)
+        clean = torch.from_numpy(np.ascontiguousarray(xyz_np[labels_np == 0])).cuda()
+        den = torch.from_numpy(np.ascontiguousarray(xyz_np[mask_np == 1])).cuda()
+        m = {}
+
+        def metrics():
+            m.update(d.eval_metrics(clean, den, stream=stream))
+        ms = timed(metrics, 3)
+        out["metrics"] = entry(len(clean) + len(den), ms, 2 * len(clean) * len(den))
+        out["metrics"].update(clean_points=len(clean), denoised_points=len(den), psnr=m["psnr"],
+                              chamfer=m["chamfer"], mse=m["mse"])
+        kept = {}
+
+        def baseline():
+            kept["n"] = d.run_baseline(xyz, stream=stream)["keep"]
+        ms = timed(baseline, 3)
+        out["baseline"] = entry(n, ms, n * n)
+        out["baseline"]["kept"] = int(kept["n"].sum().item())
+    finally:
+        d.close()
+    obj, _ = synth.object_cloud(seed=0)
+    xo = torch.from_numpy(obj).cuda()
+    d = Denoiser(max_points=len(obj))
+    try:
+        Po = Params(k=16, leaf_capacity=0xFFFFFFFF)
+        r = d.run(xo, Po, stream=stream)
+        ms = timed(lambda: d.run(xo, Po, mask=r.mask, score=r.score, stage=r.stage, stream=stream), 2)
+        out["octree_off"] = entry(len(obj), ms, d.stats()["knn_pairs"])
+    finally:
+        d.close()
+    return out
 
 
 def run_batched(args, stream, flush):
@@ -701,6 +803,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serving-frames", type=int, default=2000)
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the variants and evaluation-call timings")
     ap.add_argument("--batch-profile", action="store_true",
                     help="run only the batched LiDAR workload at fixed knobs (for profiling)")
     args = ap.parse_args()

@@ -323,8 +323,8 @@ int enqueue(denoise_ctx *c, const float *xyz_dev, uint32_t n, uint32_t nframes, 
       xa.dbg = *dbg;
       xa.use_dbg = 1;
     }
-    if (launch_xleaf_knn(xa, c->num_sms, st)) return cuda_fail();
-    ++launches;
+    xa.unit_start = c->d_vals[0];  // free after the front end
+    if (launch_xleaf_knn(xa, c->num_sms, st, &launches)) return cuda_fail();
     la.xphase = 3;
   }
   if (launch_leaf(la, c->num_sms, st, &launches, c->side_stream, c->fork_ev, c->join_ev)) return cuda_fail();

@@ -90,6 +90,7 @@ struct Counters {
   uint32_t leaf_work3;                   // the same for the launch that takes the small leaves
   uint32_t split_leaf;                   // first index of the largest-first order with leaves of <= kSmallLeaf points
   uint32_t xleaf_work;                   // cross-leaf kNN work counter
+  uint32_t x_units;                      // cross-leaf kNN work units (leaf, 64 queries)
   uint32_t tile_work[kMaxPasses];        // radix-pass tile counters
   uint32_t cls_count[kLeafClasses];      // leaves per size class
   uint32_t cls_cursor[kLeafClasses];     // fill cursors of the class-ordered leaf list
@@ -227,10 +228,11 @@ struct XleafArgs {
   uint32_t *xnbr;
   float *xr2;
   uint32_t *xkeff;
+  uint32_t *unit_start;  // [n_leaves] scratch: first work unit of each leaf (K <= 32)
   denoise_debug dbg;
   int use_dbg;
 };
-int launch_xleaf_knn(const XleafArgs &a, int num_sms, cudaStream_t st);
+int launch_xleaf_knn(const XleafArgs &a, int num_sms, cudaStream_t st, int *launches);
 
 int leaf_kmax(uint32_t k);
 size_t leaf_smem_bytes(uint32_t lmax, int kmax);
