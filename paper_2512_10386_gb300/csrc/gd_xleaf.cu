@@ -342,21 +342,26 @@ __global__ void __launch_bounds__(kXWThreads) k_xleaf_knn_warp(const XleafArgs A
             const bool in = v < len;
             const float4 pc = in ? s_c[v] : make_float4(0.f, 0.f, 0.f, 0.f);
             const uint32_t pp = in ? s_p[v] : 0xFFFFFFFFu;
-            const unsigned long long lo = (unsigned long long)__float_as_uint(pc.w);
+            const uint32_t gi = __float_as_uint(pc.w);
+            // every query's test first (independent), against the high word of its
+            // threshold: a candidate with larger d^2 cannot improve the list
+            uint32_t db[kXWQ], mm[kXWQ];
 #pragma unroll
             for (int j = 0; j < kXWQ; ++j) {
-              if (!((act >> j) & 1u)) continue;  // warp-uniform
-              unsigned long long key = ~0ull;
-              if (pp != 0xFFFFFFFFu && pp != qpos[j]) {
-                const float dx = __fsub_rn(pc.x, qx[j]), dy = __fsub_rn(pc.y, qy[j]), dz = __fsub_rn(pc.z, qz[j]);
-                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                key = ((unsigned long long)__float_as_uint(d2) << 32) | lo;
-              }
-              uint32_t m = __ballot_sync(0xFFFFFFFFu, key < thr[j]);
-              while (m) {  // the chunk's improving keys one by one (the threshold falls as they go in)
+              const float dx = __fsub_rn(pc.x, qx[j]), dy = __fsub_rn(pc.y, qy[j]), dz = __fsub_rn(pc.z, qz[j]);
+              db[j] = __float_as_uint(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
+              const bool ok = ((act >> j) & 1u) && pp != 0xFFFFFFFFu && pp != qpos[j] &&
+                              db[j] <= (uint32_t)(thr[j] >> 32);
+              mm[j] = __ballot_sync(0xFFFFFFFFu, ok);
+            }
+#pragma unroll
+            for (int j = 0; j < kXWQ; ++j) {
+              uint32_t m = mm[j];
+              while (m) {  // the exact (d^2, index) keys in lane order; the threshold falls as they go in
                 const int b = __ffs(m) - 1;
                 m &= m - 1u;
-                const unsigned long long K = __shfl_sync(0xFFFFFFFFu, key, b);
+                const unsigned long long K = ((unsigned long long)__shfl_sync(0xFFFFFFFFu, db[j], b) << 32) |
+                                             __shfl_sync(0xFFFFFFFFu, gi, b);
                 const uint32_t P = __shfl_sync(0xFFFFFFFFu, pp, b);
                 if (K < thr[j]) xw_insert(Lk[j], Lp[j], thr[j], K, P, lane, keff);
               }
