@@ -90,7 +90,7 @@ struct Counters {
   uint32_t leaf_work3;                   // the same for the launch that takes the small leaves
   uint32_t split_leaf;                   // first index of the largest-first order with leaves of <= kSmallLeaf points
   uint32_t xleaf_work;                   // cross-leaf kNN work counter
-  uint32_t x_units;                      // cross-leaf kNN work units (leaf, 64 queries)
+  uint32_t x_units;                      // cross-leaf kNN work units (leaf, 32 queries)
   uint32_t tile_work[kMaxPasses];        // radix-pass tile counters
   uint32_t cls_count[kLeafClasses];      // leaves per size class
   uint32_t cls_cursor[kLeafClasses];     // fill cursors of the class-ordered leaf list

@@ -14,12 +14,12 @@
 // positions), the floored r_K^2 and k_eff.  The per-leaf gate, median, score and
 // selection then run in the fused leaf kernel's cross-leaf phase.
 //
-// For K <= 32 one warp takes one query at a time (k_xleaf_knn_warp): the sorted
-// list of its k_eff smallest keys is spread over the lanes (lane t holds rank t),
-// the warp reads 32 candidates a step (coalesced; a leaf's candidates stay in L1
-// for all its queries), and each candidate below the current k_eff-th key is
-// inserted by one shuffle step of the whole list.  Larger K keep the per-thread
-// list (k_xleaf_knn).
+// For K <= 32 the work is split into units of (leaf, 32 queries) (k_xleaf_units,
+// k_xleaf_knn_warp): a CTA stages the unit's candidates in shared memory tile by
+// tile, each warp keeps the sorted lists of 4 queries spread over its lanes (lane
+// t holds rank t), tests 32 candidates a step against all 4, and inserts each
+// candidate below a query's current k_eff-th key by one shuffle step of that
+// list.  Larger K keep the per-thread list (k_xleaf_knn).
 #include <cuda_runtime.h>
 
 #include "gd_common.cuh"
@@ -179,10 +179,11 @@ __global__ void __launch_bounds__(kXThreads) k_xleaf_knn(const XleafArgs A) {
   }
 }
 
-// ---- K <= 32: work units of (leaf, 64 queries); one warp keeps 8 queries' lists
+// ---- K <= 32: work units of (leaf, 32 queries); one warp keeps 4 queries' lists
 constexpr int kXWThreads = 256;                 // 8 warps
-constexpr int kXWQ = 8;                         // queries per warp
-constexpr int kXWUnit = kXWQ * kXWThreads / 32; // queries per unit (64)
+constexpr int kXWQ = 4;                         // queries per warp (8 with 2 CTAs per SM: 13.3 vs 9.0 ms)
+constexpr int kXWCtas = 4;                      // CTAs per SM (3: 9.6 ms)
+constexpr int kXWUnit = kXWQ * kXWThreads / 32; // queries per unit (32)
 constexpr int kXWTile = 2048;                   // candidates staged per round
 
 // unit_start[l] = first work unit of leaf l (ceil(count / kXWUnit) units per leaf),
@@ -242,7 +243,7 @@ __device__ __forceinline__ void xw_insert(unsigned long long &Lk, uint32_t &Lp, 
 }
 
 template <bool kRec>
-__global__ void __launch_bounds__(kXWThreads) k_xleaf_knn_warp(const XleafArgs A) {
+__global__ void __launch_bounds__(kXWThreads, kXWCtas) k_xleaf_knn_warp(const XleafArgs A) {
   __shared__ float4 s_c[kXWTile];
   __shared__ uint32_t s_p[kXWTile];   // candidate position, 0xFFFFFFFF: not in P_1
   __shared__ uint32_t s_rng[27][2];
@@ -412,7 +413,7 @@ int launch_x(const XleafArgs &a, int num_sms, cudaStream_t st, int *launches) {
   cudaError_t e;
   if (a.k <= 32) {
     e = launch_pdl(k_xleaf_units, 1, 1024, 0, st, a.leaves, a.ctr, a.unit_start);
-    if (e == cudaSuccess) e = launch_pdl(k_xleaf_knn_warp<kRec>, num_sms * 2, kXWThreads, 0, st, a);
+    if (e == cudaSuccess) e = launch_pdl(k_xleaf_knn_warp<kRec>, num_sms * kXWCtas, kXWThreads, 0, st, a);
     if (launches) *launches += 2;
   } else {
     e = go(k_xleaf_knn<64, kRec>);
